@@ -1,0 +1,100 @@
+"""Coupling-matrix entries from the free-space dyadic Green's function (FP64).
+
+Paper: Eq. n6 gives the scalar Helmholtz kernel g = exp(-i k0 R) / (4 pi R); Eq. nNt
+defines the N operator built on it; Sec. III.A says each column of the coupling
+matrix is the concatenation of q per-component vectors over the voxels, reshaped
+column-major into n1 x n2 x n3 tensors (Fig. 2).
+
+Point-matched form used here (one quadrature point per voxel and per segment):
+    Z[(k, v), e] = h^3 * len_e * [ G(r_v - c_e) t_e ]_k,   G = (I + grad grad / k0^2) g
+with, for R = |r_v - c_e|, Rhat the unit vector and x = k0 R,
+    G = g * [ (1 - i/x - 1/x^2) I + (-1 + 3i/x + 3/x^2) Rhat Rhat^T ].
+The closed form follows from grad grad g = g'' Rhat Rhat + (g'/R)(I - Rhat Rhat).
+Row index (k, v) -> k*n_v + v  (Algorithm 1: Y = [Y^1; ...; Y^q]).
+"""
+import numpy as np
+
+C0 = 299_792_458.0
+
+
+def wavenumber(freq_hz: float) -> float:
+    return 2.0 * np.pi * freq_hz / C0
+
+
+def scalar_green(R: np.ndarray, k0: float) -> np.ndarray:
+    """Eq. n6."""
+    return np.exp(-1j * k0 * R) / (4.0 * np.pi * R)
+
+
+def dyadic_green(r_obs: np.ndarray, r_src: np.ndarray, k0: float) -> np.ndarray:
+    """(I + grad grad / k0^2) g evaluated at r_obs - r_src; inputs (..., 3), output (..., 3, 3)."""
+    Rv = np.asarray(r_obs, dtype=np.float64) - np.asarray(r_src, dtype=np.float64)
+    R = np.asarray(np.sqrt((Rv * Rv).sum(axis=-1)))
+    Rh = Rv / R[..., None]
+    x = k0 * R
+    g = np.asarray(scalar_green(R, k0))
+    a = np.asarray(1.0 - 1j / x - 1.0 / x ** 2)
+    b = np.asarray(-1.0 + 3j / x + 3.0 / x ** 2)
+    eye = np.eye(3)
+    return g[..., None, None] * (a[..., None, None] * eye + b[..., None, None] * Rh[..., :, None] * Rh[..., None, :])
+
+
+def voxel_centres(n1: int, n2: int, n3: int, h: float) -> np.ndarray:
+    """(n_v, 3) centres, v = i1 + n1*(i2 + n2*i3), centred at the origin."""
+    a1 = (np.arange(n1) - (n1 - 1) / 2.0) * h
+    a2 = (np.arange(n2) - (n2 - 1) / 2.0) * h
+    a3 = (np.arange(n3) - (n3 - 1) / 2.0) * h
+    x = np.broadcast_to(a1[None, None, :], (n3, n2, n1)).reshape(-1)
+    y = np.broadcast_to(a2[None, :, None], (n3, n2, n1)).reshape(-1)
+    z = np.broadcast_to(a3[:, None, None], (n3, n2, n1)).reshape(-1)
+    return np.stack([x, y, z], axis=1)
+
+
+def voxel_mask(n1, n2, n3, h, mask_radius) -> np.ndarray:
+    """True for voxels kept; voxels with sqrt(x^2+y^2) > mask_radius are dropped (0 = keep all)."""
+    r = voxel_centres(n1, n2, n3, h)
+    if mask_radius <= 0:
+        return np.ones(r.shape[0], dtype=bool)
+    return np.sqrt(r[:, 0] ** 2 + r[:, 1] ** 2) <= mask_radius
+
+
+def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_radius=0.0,
+                     rows=None) -> np.ndarray:
+    """Dense columns Z[:, cols] of the (q*n_v) x m coupling matrix, complex128, column-major.
+
+    rows: optional subset of voxel indices v; the result then has q*len(rows) rows
+    ordered (k, row-position).
+    """
+    assert q == 3
+    n1, n2, n3 = n
+    k0 = wavenumber(freq_hz)
+    rv = voxel_centres(n1, n2, n3, h)
+    keep = voxel_mask(n1, n2, n3, h, mask_radius)
+    if rows is not None:
+        rows = np.asarray(rows)
+        rv = rv[rows]
+        keep = keep[rows]
+    nv = rv.shape[0]
+    cols = np.atleast_1d(np.asarray(cols))
+    out = np.zeros((q * nv, cols.size), dtype=np.complex128, order="F")
+    for jj, e in enumerate(cols):
+        G = dyadic_green(rv, centre[e][None, :], k0)          # (nv, 3, 3)
+        f = G @ tangent[e]                                     # (nv, 3)
+        f *= h ** 3 * length[e]
+        f[~keep] = 0.0
+        for k in range(q):
+            out[k * nv:(k + 1) * nv, jj] = f[:, k]
+    return out
+
+
+def assemble_row(n, h, centre, tangent, length, freq_hz, row, q=3, mask_radius=0.0) -> np.ndarray:
+    """One row Z[row, :] (all m columns), row = k*n_v + v."""
+    n1, n2, n3 = n
+    nv = n1 * n2 * n3
+    k, v = divmod(int(row), nv)
+    rv = voxel_centres(n1, n2, n3, h)[v]
+    if not voxel_mask(n1, n2, n3, h, mask_radius)[v]:
+        return np.zeros(length.shape[0], dtype=np.complex128)
+    G = dyadic_green(rv[None, :], centre, wavenumber(freq_hz))   # (m, 3, 3)
+    f = np.einsum("eab,eb->ea", G, tangent) * (h ** 3 * length)[:, None]
+    return f[:, k].copy()

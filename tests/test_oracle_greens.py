@@ -1,0 +1,119 @@
+"""Pins of the oracle's dyadic Green's function and column assembly (Eq. n6, Eq. nNt, Sec. III.A).
+
+Each check compares against something other than the oracle's own closed form:
+finite differences of the scalar kernel, textbook on-axis values, symmetry,
+reciprocity and the far-field limit.
+"""
+import numpy as np
+import pytest
+
+from oracle import greens
+from paper_2103_06393_gb300 import inputs
+
+K0 = greens.wavenumber(298.2e6)
+
+
+def test_wavenumber_value():
+    # k0 = 2 pi f / c at 298.2 MHz
+    assert abs(K0 - 6.249807) < 1e-5
+    assert abs(2 * np.pi / K0 - 1.005340) < 1e-5
+
+
+def _fd_dyadic(r, k0, step=1e-4):
+    """(I + grad grad / k0^2) g by central second differences of the scalar kernel only."""
+    def g(x):
+        return greens.scalar_green(np.linalg.norm(x), k0)
+    H = np.zeros((3, 3), dtype=complex)
+    e = np.eye(3) * step
+    for a in range(3):
+        for b in range(3):
+            H[a, b] = (g(r + e[a] + e[b]) - g(r + e[a] - e[b]) - g(r - e[a] + e[b]) + g(r - e[a] - e[b])) / (4 * step * step)
+    return g(r) * np.eye(3) + H / k0 ** 2
+
+
+@pytest.mark.parametrize("r", [np.array([0.05, -0.03, 0.02]), np.array([0.2, 0.1, -0.3]), np.array([0.0, 0.0, 0.4])])
+def test_dyadic_matches_finite_differences(r):
+    G = greens.dyadic_green(r, np.zeros(3), K0)
+    Gfd = _fd_dyadic(r, K0, step=1e-4 * np.linalg.norm(r))
+    assert np.max(np.abs(G - Gfd)) / np.max(np.abs(G)) < 1e-6
+
+
+def test_on_axis_closed_form():
+    R = 0.3
+    G = greens.dyadic_green(np.array([0, 0, R]), np.zeros(3), K0)
+    x = K0 * R
+    g = np.exp(-1j * x) / (4 * np.pi * R)
+    assert np.isclose(G[2, 2], g * (2j / x + 2 / x ** 2), rtol=1e-13)
+    assert np.isclose(G[0, 0], g * (1 - 1j / x - 1 / x ** 2), rtol=1e-13)
+    assert np.isclose(G[1, 1], G[0, 0], rtol=1e-13)
+    off = [G[0, 1], G[0, 2], G[1, 2], G[1, 0], G[2, 0], G[2, 1]]
+    assert max(abs(v) for v in off) < 1e-15 * abs(G[0, 0])
+
+
+def test_symmetry_and_reciprocity():
+    rng = np.random.default_rng(3)
+    a, b = rng.normal(size=3) * 0.1, rng.normal(size=3) * 0.1 + 0.2
+    G1 = greens.dyadic_green(a, b, K0)
+    G2 = greens.dyadic_green(b, a, K0)
+    assert np.allclose(G1, G1.T, rtol=1e-14, atol=0)
+    assert np.allclose(G1, G2, rtol=1e-14, atol=0)
+
+
+def test_far_field_is_transverse():
+    # for k0 R >> 1, G -> g (I - Rhat Rhat^T)
+    r = np.array([300.0, 400.0, 0.0])
+    G = greens.dyadic_green(r, np.zeros(3), K0)
+    R = np.linalg.norm(r)
+    rh = r / R
+    g = greens.scalar_green(R, K0)
+    approx = g * (np.eye(3) - np.outer(rh, rh))
+    assert np.max(np.abs(G - approx)) / abs(g) < 3.0 / (K0 * R)
+
+
+def test_voxel_ordering_and_centres():
+    c = greens.voxel_centres(3, 4, 5, 0.01)
+    v = 2 + 3 * (1 + 4 * 3)     # i1=2, i2=1, i3=3
+    assert np.allclose(c[v], [(2 - 1) * 0.01, (1 - 1.5) * 0.01, (3 - 2) * 0.01])
+
+
+def test_assembly_entry_by_hand_and_row_column_consistency():
+    w = inputs.scaled_workload("tiny", (5, 6, 7), m=8)
+    g, s = w.grid, w.segments
+    Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m))
+    nv = g.nv
+    # one entry from the on-axis/general closed form written per component
+    v, e, k = 17, 3, 1
+    rv = greens.voxel_centres(*g.shape, g.h)[v]
+    R = rv - s.centre[e]
+    Rn = np.linalg.norm(R)
+    rh = R / Rn
+    x = K0 * Rn
+    gg = np.exp(-1j * x) / (4 * np.pi * Rn)
+    val = gg * ((1 - 1j / x - 1 / x ** 2) * s.tangent[e][k]
+                + (-1 + 3j / x + 3 / x ** 2) * rh[k] * (rh @ s.tangent[e]))
+    assert np.isclose(Z[k * nv + v, e], g.h ** 3 * s.length[e] * val, rtol=1e-13)
+    row = greens.assemble_row(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, k * nv + v)
+    assert np.allclose(row, Z[k * nv + v, :], rtol=1e-14, atol=0)
+
+
+def test_assembly_linear_in_tangent():
+    g = inputs.Grid(4, 5, 6, 0.01)
+    c = np.array([[0.2, 0.05, 0.0]])
+    t1, t2 = np.array([[1.0, 0, 0]]), np.array([[0, 0.6, 0.8]])
+    ln = np.array([0.01])
+    z1 = greens.assemble_columns(g.shape, g.h, c, t1, ln, 3e8, [0])
+    z2 = greens.assemble_columns(g.shape, g.h, c, t2, ln, 3e8, [0])
+    z12 = greens.assemble_columns(g.shape, g.h, c, 0.3 * t1 + 0.7 * t2, ln, 3e8, [0])
+    assert np.allclose(z12, 0.3 * z1 + 0.7 * z2, rtol=1e-13, atol=0)
+
+
+def test_mask_zeroes_outer_voxels():
+    g = inputs.Grid(10, 10, 4, 0.01, mask_radius=0.04)
+    c = np.array([[0.3, 0.0, 0.0]])
+    t = np.array([[0, 1.0, 0]])
+    z = greens.assemble_columns(g.shape, g.h, c, t, np.array([0.01]), 3e8, [0], mask_radius=g.mask_radius)
+    keep = greens.voxel_mask(*g.shape, g.h, g.mask_radius)
+    assert keep.sum() < g.nv
+    for k in range(3):
+        seg = z[k * g.nv:(k + 1) * g.nv, 0]
+        assert np.all(seg[~keep] == 0) and np.all(seg[keep] != 0)
