@@ -1,0 +1,194 @@
+/*
+ * zbc.h -- C ABI of the Tucker-compressed VSIE coupling-matrix library (GB300, sm_103a).
+ *
+ * The library implements the hot path of Giannakopoulos et al., "Compression of
+ * volume-surface integral equation matrices via Tucker decomposition for magnetic
+ * resonance applications" (arXiv 2103.06393): column assembly of the coil-body
+ * coupling matrix Z (q*n_v x m), column-wise Tucker compression (Sec. III.A), ACA
+ * and Algorithm 3 (Sec. III.C), and the products Y = Z X (Algorithm 1) and
+ * Psi = Z^H Phi (Algorithm 2, Sec. III.B).
+ *
+ * Conventions shared by every call
+ *  - Complex numbers are interleaved (re, im): complex64 = 2 x float, complex128 = 2 x double.
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *  - Voxel index v = i1 + n1*(i2 + n2*i3) (column-major reshape of a column, Fig. 2);
+ *    row index of Z is k*n_v + v for field component k = 0..q-1 (Y = [Y^1; ...; Y^q]).
+ *  - Voxel centres are ((i - (n-1)/2) * h) per axis (grid centred at the origin).
+ *  - Every pointer is a DEVICE pointer owned by the caller unless its name ends in
+ *    _host.  The library never frees caller memory.
+ *  - Every call returns an int status (ZBC_OK = 0, negative on error); on error
+ *    zbc_last_error() returns a message (thread-local, valid until the next call on
+ *    the same thread).  No C++ exception crosses this boundary.
+ *  - Calls taking a stream enqueue their kernels on it and return without waiting,
+ *    except where the comment says the call synchronises (compression sizes its
+ *    output from device results and therefore waits).
+ *  - A zbc_handle is library-owned, immutable after creation except where noted, and
+ *    must not be used by two calls that overlap on the GPU (the product calls keep
+ *    per-handle workspace).
+ */
+#ifndef ZBC_H
+#define ZBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* zbc_stream;
+
+enum {
+  ZBC_OK = 0,
+  ZBC_EINVAL = -1,    /* bad argument: null pointer, size out of range, ld too small */
+  ZBC_ENOMEM = -2,    /* device or host allocation failed */
+  ZBC_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  ZBC_ETOL = -4,      /* a tolerance could not be met (fallback exhausted) */
+  ZBC_ETIMEOUT = -5,  /* a bounded device wait gave up (kernel returned an error status) */
+  ZBC_ENAN = -6,      /* NaN or Inf found in an input */
+  ZBC_EIO = -7        /* file read/write failed or file is not a zbc handle */
+};
+
+typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
+
+/* Arithmetic form of the product kernels.
+ * FP32_SIMT : complex FP32 on CUDA cores (the plain form).
+ * TF32X3    : tensor cores, tcgen05 kind::tf32, each operand split hi+lo, 3 products, FP32 accumulation.
+ * BF16X3    : tensor cores, tcgen05 kind::f16 with bf16 operands split into 3 terms
+ *             (hi+mid+lo), the 6 products above 2^-24, FP32 accumulation. */
+typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2 } zbc_precision;
+
+typedef enum { ZBC_HOSVD = 0, ZBC_RANDOMIZED_LEARNED = 1, ZBC_RANDOMIZED_FIXED = 2 } zbc_tucker_method;
+
+typedef enum { ZBC_ACA_DENSE_U = 0, ZBC_ACA_ALG3 = 1 } zbc_aca_mode;
+
+typedef struct {
+  int32_t n1, n2, n3;   /* voxels per axis */
+  double h;             /* voxel edge (m) */
+  double mask_radius;   /* voxels with sqrt(x^2+y^2) > mask_radius are zero rows; <= 0: no mask */
+} zbc_grid;
+
+typedef struct {
+  int32_t m;              /* number of segments (columns of Z) */
+  const double* centre;   /* device, m x 3 row-major (x,y,z per segment), metres */
+  const double* tangent;  /* device, m x 3 row-major, unit vectors */
+  const double* length;   /* device, m, metres */
+} zbc_segments;
+
+typedef struct zbc_handle zbc_handle;
+
+typedef struct {
+  int32_t n1, n2, n3, q;
+  int32_t M;          /* stored columns: m (Tucker only) or r_c (ACA + Tucker) */
+  int32_t m;          /* columns of Z */
+  int32_t has_v;      /* 1 if Z = U V^H with V (m x M) stored dense */
+  int32_t max_rank;   /* largest Tucker rank over all tensors and modes */
+  int64_t pool_bytes; /* bytes of cores + factors (complex64) */
+  int64_t v_bytes;    /* bytes of V (complex64) */
+} zbc_info;
+
+typedef struct {
+  int32_t n_tensors;   /* tensors compressed by this call */
+  int32_t n_fallback;  /* randomized tensors that failed the check and were redone by HOSVD */
+  int32_t max_rank;
+  double max_rel_err;  /* largest certified relative Frobenius error bound over the tensors */
+} zbc_compress_stats;
+
+/* Last error message of this thread ("" if none). */
+const char* zbc_last_error(void);
+
+/* Library version string. */
+const char* zbc_version(void);
+
+/*
+ * vsie_assemble_columns -- columns of the coupling matrix (Sec. III.A; Eq. n6, Eq. nNt).
+ *   Z[(k,v), e] = h^3 len_e [ (I + grad grad / k0^2) g(r_v - c_e) t_e ]_k,
+ *   g(R) = exp(-i k0 R) / (4 pi R),  k0 = 2 pi freq_hz / 299792458,
+ * i.e. the point-matched (one point per voxel and per segment) dyadic kernel, evaluated
+ * in FP64.  q must be 3 (piecewise-constant basis, three field components).
+ *   cols : device int32[ncols], column indices e in [0, s->m)
+ *   out  : device, (q*n_v) x ncols, column-major, leading dimension ld >= q*n_v, dtype dt
+ * Masked voxels (grid mask_radius) give exact zeros.  A segment centre closer than
+ * 1e-12 m to a voxel centre is a caller error that the kernel does not check (R = 0).
+ * Entries of cols outside [0, s->m) produce an all-zero output column.
+ */
+int vsie_assemble_columns(const zbc_grid* g, const zbc_segments* s, double freq_hz,
+                          const int32_t* cols, int ncols, int q,
+                          void* out, int64_t ld, zbc_dtype dt, zbc_stream stream);
+
+/*
+ * tucker_compress -- column-wise Tucker compression (Sec. III.A, Fig. 2; truncated HOSVD of
+ * Sec. II.B.1 with De Lathauwer's bound).
+ *   cols   : device, (q*n_v) x ncols column-major (ld >= q*n_v), dtype in_dt
+ *   tol    : per-tensor relative Frobenius tolerance; mode g keeps the smallest r_g with
+ *            sum_{i>r_g} sigma_i^2 <= (tol^2/3) ||A||_F^2 (so ||A - A~||_F <= tol ||A||_F)
+ *   method : ZBC_HOSVD (FP64 two-pass Gram + Jacobi eigensolver per unfolding), or one of the
+ *            randomized methods (declared with the rank model, see zbc_mlp.h)
+ *   out    : *out == NULL -> a new handle holding these ncols columns;
+ *            *out != NULL -> the columns are appended to that handle (same grid and q)
+ *   stats_host : optional (may be NULL)
+ * Cores and factors are stored complex64.  Synchronises the stream (ranks size the storage).
+ */
+int tucker_compress(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q,
+                    zbc_dtype in_dt, double tol, zbc_tucker_method method,
+                    zbc_handle** out, zbc_compress_stats* stats_host, zbc_stream stream);
+
+/*
+ * zbc_matvec -- Y = Z X (Algorithm 1, Sec. III.B).  With ACA storage (Z = U V^H) the library
+ * first forms X' = V^H X (r_c x p) and runs Algorithm 1 on U (Sec. III.B, last paragraph).
+ *   X : device complex64, m x p, column-major, ldx >= m
+ *   Y : device complex64, (q*n_v) x p, column-major, ldy >= q*n_v; overwritten
+ *   p : 1 .. 1024 right-hand sides
+ */
+int zbc_matvec(const zbc_handle* h, const void* X, int64_t ldx, int p, void* Y, int64_t ldy,
+               zbc_precision prec, zbc_stream stream);
+
+/*
+ * zbc_rmatvec -- Psi = Z^H Phi (Algorithm 2, Sec. III.B).  With ACA storage the product on U
+ * is followed by Psi = V Psi'.
+ *   Phi : device complex64, (q*n_v) x p, ldphi >= q*n_v
+ *   Psi : device complex64, m x p, ldpsi >= m; overwritten
+ * Partial sums over voxel tiles are reduced in a fixed order (deterministic).
+ */
+int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi,
+                int64_t ldpsi, zbc_precision prec, zbc_stream stream);
+
+/* Release a handle and its device memory (NULL is accepted). */
+int zbc_free(zbc_handle* h);
+
+/* Shape and storage summary of a handle. */
+int zbc_get_info(const zbc_handle* h, zbc_info* info_host);
+
+/*
+ * zbc_memory_bytes -- storage model of Table II (Sec. III.A) for this handle, in bytes at
+ * complex64: tucker = sum over tensors of (r1 r2 r3 + n1 r1 + n2 r2 + n3 r3) * 8,
+ * v = m * r_c * 8 (0 without ACA), full_equiv = q * n_v * m * 8.
+ */
+int zbc_memory_bytes(const zbc_handle* h, int64_t* tucker_host, int64_t* v_host, int64_t* full_equiv_host);
+
+/*
+ * Host import/export of the compressed storage (tests, checkpoints).
+ * Tensor t = j*q + k (column j, component k) has ranks ranks_host[3t..3t+2] = (r1, r2, r3) and
+ * occupies, in this order, complex64 entries:
+ *   core G[a + r1*(b + r2*c)]            (r1*r2*r3)
+ *   U1[i1 + n1*a], U2[i2 + n2*b], U3[i3 + n3*c]   (n_g x r_g column-major each)
+ * consecutively in pool_host (tensors in order t = 0, 1, ...).  v_host is m x M column-major
+ * complex64 or NULL (no ACA).  ranks must be in [1, n_g].
+ */
+int zbc_create_from_host(const zbc_grid* g, int q, int M, int m, const int32_t* ranks_host,
+                         const void* pool_host, int64_t pool_elems, const void* v_host,
+                         zbc_handle** out);
+/* ranks_host: int32[3*M*q]; pool_host: complex64[pool_elems] (query sizes with zbc_get_info:
+ * pool_elems = pool_bytes/8); v_host: complex64[m*M] or NULL.  Synchronises the device. */
+int zbc_export_host(const zbc_handle* h, int32_t* ranks_host, void* pool_host, void* v_host);
+
+/* Checkpoint: flat little-endian file "ZBC1" + header + ranks + pool + V.  zbc_load creates
+ * a new handle on the current device. */
+int zbc_save(const zbc_handle* h, const char* path);
+int zbc_load(const char* path, zbc_handle** out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZBC_H */

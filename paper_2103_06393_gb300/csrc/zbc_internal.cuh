@@ -1,0 +1,126 @@
+// Internal definitions shared by the translation units of libzbc (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/zbc.h"
+
+namespace zbc {
+
+// ---------------------------------------------------------------------------------------------
+// error reporting: thread-local message, status codes only across the ABI
+// ---------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define ZBC_TRY_CUDA(expr)                                                                  \
+  do {                                                                                      \
+    cudaError_t _e = (expr);                                                                \
+    if (_e != cudaSuccess) {                                                                \
+      ::zbc::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__,     \
+                       __LINE__);                                                           \
+      return _e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;                       \
+    }                                                                                       \
+  } while (0)
+
+#define ZBC_CHECK_ARG(cond, ...)                                                            \
+  do {                                                                                      \
+    if (!(cond)) {                                                                          \
+      ::zbc::set_error(__VA_ARGS__);                                                        \
+      return ZBC_EINVAL;                                                                    \
+    }                                                                                       \
+  } while (0)
+
+#define ZBC_TRY(expr)             \
+  do {                            \
+    int _s = (expr);              \
+    if (_s != ZBC_OK) return _s;  \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// device workspace that grows on demand and is freed with its owner
+// ---------------------------------------------------------------------------------------------
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);  // grow-only; contents are not preserved
+  void release();
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// ---------------------------------------------------------------------------------------------
+// the compressed coupling matrix
+// ---------------------------------------------------------------------------------------------
+// Tensor t = j*q + k.  Pool layout per tensor (complex64): core G[a + r1(b + r2 c)], then
+// U1 (n1 x r1), U2 (n2 x r2), U3 (n3 x r3) column-major.
+struct TensorDesc {
+  int64_t off;        // offset of the core in the pool (complex64 elements)
+  int32_t r1, r2, r3;
+  float scale_log2;   // floor(log2 ||G||_F), used for the per-column scaling of the fp16 path
+};
+
+struct TcPack;  // tensor-core operand staging, built lazily (products_tc.cu)
+
+struct Handle {
+  int n1 = 0, n2 = 0, n3 = 0, q = 0;
+  int M = 0;          // stored columns
+  int m = 0;          // columns of Z
+  bool has_v = false;
+  std::vector<int32_t> ranks;      // 3*M*q
+  std::vector<TensorDesc> desc;    // M*q
+  int64_t pool_elems = 0;
+  float2* d_pool = nullptr;        // complex64 cores + factors
+  TensorDesc* d_desc = nullptr;    // device copy of desc
+  float2* d_v = nullptr;           // m x M complex64 (ACA) or null
+  int max_rank = 0;
+  // per-handle workspaces of the product calls (not thread-safe: one call at a time)
+  DevBuf work_partial;   // adjoint partial sums
+  DevBuf work_x;         // X' = V^H X (ACA), scaled operands
+  DevBuf work_misc;
+  TcPack* tc = nullptr;
+  ~Handle();
+  int64_t nv() const { return (int64_t)n1 * n2 * n3; }
+  int upload();          // copy desc to device (pool already on device)
+};
+
+int handle_append(Handle* h, const std::vector<int32_t>& ranks, const float2* d_pool_new,
+                  int64_t new_elems, int ncols, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 c) {  // conj(a)*b + c
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ double2 zfma_conj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+int sm_count();
+
+}  // namespace zbc
+
+struct zbc_handle {
+  zbc::Handle h;
+};

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libzbc (argument marshalling only: every step runs in the library).
+
+Function names follow the C ABI in include/zbc.h.  Tensors are torch tensors on the GPU
+(complex64 / complex128 / int32 / float64, column-major where the ABI says so: pass
+Fortran-ordered data as the transpose of a contiguous tensor, or use the helpers here that
+allocate column-major buffers).  The library must be built (paper_2103_06393_gb300.build);
+importing this module without it raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libzbc.so")
+
+ZBC_OK, ZBC_EINVAL, ZBC_ENOMEM, ZBC_ECUDA, ZBC_ETOL, ZBC_ETIMEOUT, ZBC_ENAN, ZBC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
+C64, C128 = 0, 1
+FP32_SIMT, TF32X3, BF16X3 = 0, 1, 2
+HOSVD, RANDOMIZED_LEARNED, RANDOMIZED_FIXED = 0, 1, 2
+ACA_DENSE_U, ACA_ALG3 = 0, 1
+PRECISIONS = {"fp32_simt": FP32_SIMT, "tf32x3": TF32X3, "bf16x3": BF16X3}
+
+
+class ZbcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"zbc status {status}: {msg}")
+        self.status = status
+
+
+class zbc_grid(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("n3", C.c_int32), ("h", C.c_double),
+                ("mask_radius", C.c_double)]
+
+
+class zbc_segments(C.Structure):
+    _fields_ = [("m", C.c_int32), ("centre", C.c_void_p), ("tangent", C.c_void_p), ("length", C.c_void_p)]
+
+
+class zbc_info(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("n3", C.c_int32), ("q", C.c_int32), ("M", C.c_int32),
+                ("m", C.c_int32), ("has_v", C.c_int32), ("max_rank", C.c_int32), ("pool_bytes", C.c_int64),
+                ("v_bytes", C.c_int64)]
+
+
+class zbc_compress_stats(C.Structure):
+    _fields_ = [("n_tensors", C.c_int32), ("n_fallback", C.c_int32), ("max_rank", C.c_int32),
+                ("max_rel_err", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libzbc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "zbc_last_error": ([], C.c_char_p),
+            "zbc_version": ([], C.c_char_p),
+            "vsie_assemble_columns": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, vp, i64, i32, vp], i32),
+            "tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, i32, C.POINTER(vp),
+                                 C.POINTER(zbc_compress_stats), vp], i32),
+            "zbc_matvec": ([vp, vp, i64, i32, vp, i64, i32, vp], i32),
+            "zbc_rmatvec": ([vp, vp, i64, i32, vp, i64, i32, vp], i32),
+            "zbc_free": ([vp], i32),
+            "zbc_get_info": ([vp, C.POINTER(zbc_info)], i32),
+            "zbc_memory_bytes": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], i32),
+            "zbc_create_from_host": ([C.POINTER(zbc_grid), i32, i32, i32, vp, vp, i64, vp, C.POINTER(vp)], i32),
+            "zbc_export_host": ([vp, vp, vp, vp], i32),
+            "zbc_save": ([vp, C.c_char_p], i32),
+            "zbc_load": ([C.c_char_p, C.POINTER(vp)], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ZBC_OK:
+        raise ZbcError(status, lib().zbc_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def colmajor(rows: int, cols: int, dtype, device="cuda"):
+    """A rows x cols column-major buffer: returned as a (cols, rows) contiguous tensor whose
+    row c is column c of the matrix."""
+    import torch
+    return torch.empty((cols, rows), dtype=dtype, device=device)
+
+
+def to_colmajor(a: np.ndarray, dtype=None, device="cuda"):
+    """numpy matrix -> torch tensor holding it column-major (shape (cols, rows))."""
+    import torch
+    a = np.asarray(a)
+    if dtype is not None:
+        a = a.astype(dtype)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
+
+
+def from_colmajor(t) -> np.ndarray:
+    return t.detach().cpu().numpy().T
+
+
+def grid_struct(grid) -> zbc_grid:
+    return zbc_grid(grid.n1, grid.n2, grid.n3, grid.h, getattr(grid, "mask_radius", 0.0))
+
+
+class Handle:
+    """Owns a zbc_handle*."""
+
+    def __init__(self, ptr: C.c_void_p):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and lib is not None:
+            try:
+                lib().zbc_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+    def info(self) -> zbc_info:
+        inf = zbc_info()
+        _check(lib().zbc_get_info(self.ptr, C.byref(inf)))
+        return inf
+
+    def memory_bytes(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().zbc_memory_bytes(self.ptr, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def export(self):
+        """(ranks (M, q, 3) int32, pool complex64, V (m x M) or None)."""
+        inf = self.info()
+        ranks = np.zeros(3 * inf.M * inf.q, dtype=np.int32)
+        pool = np.zeros(inf.pool_bytes // 8, dtype=np.complex64)
+        V = np.zeros((inf.M, inf.m), dtype=np.complex64) if inf.has_v else None
+        _check(lib().zbc_export_host(self.ptr, ranks.ctypes.data_as(C.c_void_p), pool.ctypes.data_as(C.c_void_p),
+                                     V.ctypes.data_as(C.c_void_p) if V is not None else None))
+        return ranks.reshape(inf.M, inf.q, 3), pool, (V.T.copy() if V is not None else None)
+
+    def tensors(self):
+        """Unpack to the oracle's format: list over j of list over k of (G, [U1,U2,U3]) (complex128)."""
+        inf = self.info()
+        ranks, pool, V = self.export()
+        n = (inf.n1, inf.n2, inf.n3)
+        out, off = [], 0
+        for j in range(inf.M):
+            comps = []
+            for k in range(inf.q):
+                r1, r2, r3 = (int(x) for x in ranks[j, k])
+                G = pool[off:off + r1 * r2 * r3].reshape((r1, r2, r3), order="F").astype(np.complex128)
+                off += r1 * r2 * r3
+                Us = []
+                for g, r in enumerate((r1, r2, r3)):
+                    Us.append(pool[off:off + n[g] * r].reshape((n[g], r), order="F").astype(np.complex128))
+                    off += n[g] * r
+                comps.append((G, Us))
+            out.append(comps)
+        return out, V
+
+    def save(self, path: str):
+        _check(lib().zbc_save(self.ptr, path.encode()))
+
+
+def pack_tensors(tensors, n) -> tuple:
+    """Oracle format -> (ranks int32[3*M*q], pool complex64) in the ABI's host layout."""
+    ranks, parts = [], []
+    for tj in tensors:
+        for t in tj:
+            G, Us = t[0], t[1]
+            ranks.extend(G.shape)
+            parts.append(np.asarray(G).reshape(-1, order="F"))
+            for U in Us:
+                parts.append(np.asarray(U).reshape(-1, order="F"))
+    return np.array(ranks, dtype=np.int32), np.concatenate(parts).astype(np.complex64)
+
+
+def zbc_create_from_host(grid, q, tensors, V=None) -> Handle:
+    ranks, pool = pack_tensors(tensors, grid.shape if hasattr(grid, "shape") else None)
+    M = len(tensors)
+    m = M if V is None else V.shape[0]
+    vcol = None
+    if V is not None:
+        vcol = np.asfortranarray(np.asarray(V, dtype=np.complex64))
+    h = C.c_void_p()
+    g = grid_struct(grid)
+    _check(lib().zbc_create_from_host(C.byref(g), q, M, m, ranks.ctypes.data_as(C.c_void_p),
+                                      pool.ctypes.data_as(C.c_void_p), pool.size,
+                                      vcol.ctypes.data_as(C.c_void_p) if vcol is not None else None, C.byref(h)))
+    return Handle(h)
+
+
+def zbc_load(path: str) -> Handle:
+    h = C.c_void_p()
+    _check(lib().zbc_load(path.encode(), C.byref(h)))
+    return Handle(h)
+
+
+class DeviceSegments:
+    """Segments uploaded to the device (float64)."""
+
+    def __init__(self, segs, device="cuda"):
+        import torch
+        self.centre = torch.from_numpy(np.ascontiguousarray(segs.centre, dtype=np.float64)).to(device)
+        self.tangent = torch.from_numpy(np.ascontiguousarray(segs.tangent, dtype=np.float64)).to(device)
+        self.length = torch.from_numpy(np.ascontiguousarray(segs.length, dtype=np.float64)).to(device)
+        self.m = int(segs.length.shape[0])
+
+    def struct(self) -> zbc_segments:
+        return zbc_segments(self.m, self.centre.data_ptr(), self.tangent.data_ptr(), self.length.data_ptr())
+
+
+def vsie_assemble_columns(grid, dsegs: DeviceSegments, freq_hz: float, cols, out, q=3, stream=None):
+    """cols: int32 CUDA tensor; out: column-major buffer (ncols, ld) complex64/complex128."""
+    import torch
+    g = grid_struct(grid)
+    s = dsegs.struct()
+    dt = C128 if out.dtype == torch.complex128 else C64
+    _check(lib().vsie_assemble_columns(C.byref(g), C.byref(s), freq_hz, _ptr(cols), int(cols.numel()), q, _ptr(out),
+                                       out.stride(0), dt, _stream(stream)))
+    return out
+
+
+def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle | None = None, stream=None):
+    """cols: column-major buffer (ncols, ld).  Returns (Handle, stats)."""
+    import torch
+    g = grid_struct(grid)
+    dt = C128 if cols.dtype == torch.complex128 else C64
+    h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
+    st = zbc_compress_stats()
+    _check(lib().tucker_compress(_ptr(cols), cols.stride(0), cols.shape[0], C.byref(g), q, dt, tol, method,
+                                 C.byref(h), C.byref(st), _stream(stream)))
+    if append_to is not None:
+        return append_to, st
+    return Handle(h), st
+
+
+def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):
+    """X: (p, ldx) complex64 (column-major m x p); Y: (p, ldy) complex64."""
+    p = X.shape[0]
+    _check(lib().zbc_matvec(h.ptr, _ptr(X), X.stride(0), p, _ptr(Y), Y.stride(0), prec, _stream(stream)))
+    return Y
+
+
+def zbc_rmatvec(h: Handle, Phi, Psi, prec=FP32_SIMT, stream=None):
+    p = Phi.shape[0]
+    _check(lib().zbc_rmatvec(h.ptr, _ptr(Phi), Phi.stride(0), p, _ptr(Psi), Psi.stride(0), prec, _stream(stream)))
+    return Psi
