@@ -100,6 +100,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _ld(t) -> int:
+    """Leading dimension of a column-major matrix held as a (cols, rows) tensor.  A single
+    column may carry any stride for its size-1 dimension, so its ld is its row count."""
+    if t.shape[0] == 1:
+        return int(t.shape[1])
+    assert t.stride(1) == 1, "column-major buffers need unit stride within a column"
+    return int(t.stride(0))
+
+
 def colmajor(rows: int, cols: int, dtype, device="cuda"):
     """A rows x cols column-major buffer: returned as a (cols, rows) contiguous tensor whose
     row c is column c of the matrix."""
@@ -237,7 +246,7 @@ def vsie_assemble_columns(grid, dsegs: DeviceSegments, freq_hz: float, cols, out
     s = dsegs.struct()
     dt = C128 if out.dtype == torch.complex128 else C64
     _check(lib().vsie_assemble_columns(C.byref(g), C.byref(s), freq_hz, _ptr(cols), int(cols.numel()), q, _ptr(out),
-                                       out.stride(0), dt, _stream(stream)))
+                                       _ld(out), dt, _stream(stream)))
     return out
 
 
@@ -248,7 +257,7 @@ def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle
     dt = C128 if cols.dtype == torch.complex128 else C64
     h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
     st = zbc_compress_stats()
-    _check(lib().tucker_compress(_ptr(cols), cols.stride(0), cols.shape[0], C.byref(g), q, dt, tol, method,
+    _check(lib().tucker_compress(_ptr(cols), _ld(cols), cols.shape[0], C.byref(g), q, dt, tol, method,
                                  C.byref(h), C.byref(st), _stream(stream)))
     if append_to is not None:
         return append_to, st
@@ -258,11 +267,11 @@ def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle
 def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):
     """X: (p, ldx) complex64 (column-major m x p); Y: (p, ldy) complex64."""
     p = X.shape[0]
-    _check(lib().zbc_matvec(h.ptr, _ptr(X), X.stride(0), p, _ptr(Y), Y.stride(0), prec, _stream(stream)))
+    _check(lib().zbc_matvec(h.ptr, _ptr(X), _ld(X), p, _ptr(Y), _ld(Y), prec, _stream(stream)))
     return Y
 
 
 def zbc_rmatvec(h: Handle, Phi, Psi, prec=FP32_SIMT, stream=None):
     p = Phi.shape[0]
-    _check(lib().zbc_rmatvec(h.ptr, _ptr(Phi), Phi.stride(0), p, _ptr(Psi), Psi.stride(0), prec, _stream(stream)))
+    _check(lib().zbc_rmatvec(h.ptr, _ptr(Phi), _ld(Phi), p, _ptr(Psi), _ld(Psi), prec, _stream(stream)))
     return Psi
