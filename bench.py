@@ -1,0 +1,402 @@
+"""Benchmark of the hot path: Y = Z X (Algorithm 1) and Psi = Z^H Phi (Algorithm 2) on the
+Tucker-compressed coupling matrix of the 96^3-voxel, 1024-segment, 16-RHS workload
+("precision": 2 mm voxels, 8-loop cylindrical coil, HOSVD tol 1e-6, complex64 storage).
+
+One step = one Z X plus one Z^H Phi on 16 right-hand sides.  Metric = algorithmic TFLOP/s of
+the step (Table III count, complex MAC = 8 flops, summed over both products), with the step
+time and the relative error against the FP64 oracle on sampled outputs.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zbc|reference] [--prec auto|...]
+
+Multi-GPU: replicas only (each rank runs the whole workload; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "precision"
+METRIC = "Z·x and Z^H·v time (s) & TFLOP/s, batched TC vs plain FP32, rel err <= 1e-5"
+UNIT = "TFLOP/s"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------------------------
+# workload construction on the GPU (assembly + HOSVD through the C ABI)
+# ---------------------------------------------------------------------------------------------
+
+def build_handle(w, zbc, torch, batch_cols=256):
+    g, s = w.grid, w.segments
+    ds = zbc.DeviceSegments(s)
+    h = None
+    t0 = time.time()
+    for c0 in range(0, s.m, batch_cols):
+        cols = torch.arange(c0, min(s.m, c0 + batch_cols), dtype=torch.int32, device="cuda")
+        Z = zbc.colmajor(3 * g.nv, cols.numel(), torch.complex128)
+        zbc.vsie_assemble_columns(g, ds, w.freq_hz, cols, Z)
+        h, st = zbc.tucker_compress(Z, g, w.tol, append_to=h)
+        del Z
+    torch.cuda.synchronize()
+    return h, time.time() - t0
+
+
+def algorithmic_flops(h, w, p):
+    from oracle import products  # only for the count formula's ranks bookkeeping
+    ranks, _, _ = h.export()
+    inf = h.info()
+    return products.flops(ranks.reshape(-1, 3), w.grid.shape, inf.q, inf.M, p)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampling
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle checks on sampled outputs
+# ---------------------------------------------------------------------------------------------
+
+def sampled_errors(tens, w, X, Phi, Y, Psi, seed=2, nrows=512, ncols=12):
+    from oracle import products, tucker
+    g = w.grid
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(3 * g.nv, size=nrows, replace=False))
+    Yo = products.matvec_rows(tens, g.shape, X, rows)
+    ey = np.linalg.norm(Y[rows] - Yo) / np.linalg.norm(Yo)
+    cols = np.sort(rng.choice(len(tens), size=min(ncols, len(tens)), replace=False))
+    Po = np.stack([tucker.decompress_column(tens[j], g.shape).conj() @ Phi for j in cols])
+    ep = np.linalg.norm(Psi[cols] - Po) / np.linalg.norm(Po)
+    return float(ey), float(ep)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(tens, w, X, Phi, F_total, budget_s=15.0):
+    """Time the oracle's Algorithms 1 and 2 over a growing prefix of the columns until about
+    budget_s of CPU work; return (TFLOP/s scaled to the full workload, columns used)."""
+    from oracle import products
+    M = len(tens)
+    ncol = 4
+    t_used, used = 0.0, 0
+    while True:
+        sub = tens[:ncol]
+        t0 = time.perf_counter()
+        products.matvec(sub, w.grid.shape, X[:ncol])
+        products.rmatvec(sub, w.grid.shape, Phi)
+        dt = time.perf_counter() - t0
+        t_used, used = dt, ncol
+        if dt > budget_s / 3 or ncol >= M:
+            break
+        ncol = min(M, ncol * 2)
+    t_full = t_used * M / used
+    return F_total / t_full / 1e12, used, t_used
+
+
+# ---------------------------------------------------------------------------------------------
+
+def time_steps(fn, steps, flush, torch, stream):
+    times = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def run_zbc(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_06393_gb300 import inputs, zbc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = inputs.workload(WORKLOAD)
+    g = w.grid
+    p = w.p
+    h, t_build = build_handle(w, zbc, torch)
+    inf = h.info()
+    log(f"[bench] handle built in {t_build:.1f}s: M={inf.M} max_rank={inf.max_rank} pool={inf.pool_bytes/2**20:.1f} MiB")
+    F1 = algorithmic_flops(h, w, p)
+    F = 2.0 * F1
+
+    X = inputs.cn01((w.segments.m, p), seed=0).astype(np.complex64)
+    Phi = inputs.cn01((3 * g.nv, p), seed=1).astype(np.complex64)
+    Xd, Phid = zbc.to_colmajor(X), zbc.to_colmajor(Phi)
+    Yd = zbc.colmajor(3 * g.nv, p, torch.complex64)
+    Psid = zbc.colmajor(w.segments.m, p, torch.complex64)
+    flushbuf = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def flush():
+        flushbuf.fill_(1)
+
+    precs = [("fp32_simt", zbc.FP32_SIMT)]
+    for name, code in (("tf32x3", zbc.TF32X3), ("bf16x3", zbc.BF16X3)):
+        try:
+            zbc.zbc_matvec(h, Xd, Yd, code)
+            precs.append((name, code))
+        except zbc.ZbcError:
+            pass
+    if args.prec != "auto":
+        precs = [(n, c) for (n, c) in precs if n == args.prec]
+
+    tens, _ = h.tensors()
+    results = {}
+    for name, code in precs:
+        def step(code=code):
+            zbc.zbc_matvec(h, Xd, Yd, code)
+            zbc.zbc_rmatvec(h, Phid, Psid, code)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ey, ep = sampled_errors(tens, w, X, Phi, zbc.from_colmajor(Yd), zbc.from_colmajor(Psid))
+        # per-product (dominant-kernel) timing
+        tf = time_steps(lambda: zbc.zbc_matvec(h, Xd, Yd, code), max(3, args.steps // 2), flush, torch, stream)
+        ta = time_steps(lambda: zbc.zbc_rmatvec(h, Phid, Psid, code), max(3, args.steps // 2), flush, torch, stream)
+        results[name] = dict(code=code, err_y=ey, err_psi=ep, t_fwd_ms=statistics.median(tf),
+                             t_adj_ms=statistics.median(ta))
+        log(f"[bench] {name}: fwd {statistics.median(tf):.3f} ms adj {statistics.median(ta):.3f} ms "
+            f"err_y {ey:.2e} err_psi {ep:.2e}")
+
+    ok = {n: r for n, r in results.items() if max(r["err_y"], r["err_psi"]) <= 1e-5}
+    head = min(ok, key=lambda n: ok[n]["t_fwd_ms"] + ok[n]["t_adj_ms"]) if ok else "fp32_simt"
+    code = results[head]["code"]
+
+    def step():
+        zbc.zbc_matvec(h, Xd, Yd, code)
+        zbc.zbc_rmatvec(h, Phid, Psid, code)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = zbc.kernel_launches()
+    times = time_steps(step, args.steps, flush, torch, stream)
+    launches = zbc.kernel_launches() - l0
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = float(np.mean(times))
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * F / (ms * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Xh = torch.from_numpy(np.ascontiguousarray(X.T)).pin_memory()
+    Phih = torch.from_numpy(np.ascontiguousarray(Phi.T)).pin_memory()
+    Yh = torch.empty(Yd.shape, dtype=Yd.dtype).pin_memory()
+    Psih = torch.empty(Psid.shape, dtype=Psid.dtype).pin_memory()
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        Phid.copy_(Phih, non_blocking=True)
+        step()
+        Yh.copy_(Yd, non_blocking=True)
+        Psih.copy_(Psid, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    te = time_steps(e2e_step, max(3, args.steps // 2), flush, torch, stream)
+    e2e_ms = float(np.mean(te))
+    h2d = Xh.numel() * 8 + Phih.numel() * 8
+    d2h = Yh.numel() * 8 + Psih.numel() * 8
+
+    # roofline of the dominant kernel (the forward product's main kernel)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    r = results[head]
+    if head == "fp32_simt":
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        mx = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = sm_count * 128 * 2 * mx * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": F1 / (r["t_fwd_ms"] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {mx:.0f} MHz",
+                "kernel": "matvec_simt_kernel", "traffic": None}
+    else:
+        mult = 6.0
+        bf = peaks.get("bf16_tflops", 1900.0)
+        peak = bf / mult
+        roof = {"bound": "tensor", "achieved": F1 / (r["t_fwd_ms"] * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"measured bf16 {bf} TFLOP/s / 6 real products per complex-split MAC",
+                "kernel": "matvec_tc_kernel", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, used, t_used = oracle_sample_rate(tens, w, X.astype(np.complex128), Phi.astype(np.complex128), F)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle Algorithms 1+2 over {used} of {inf.M} columns ({t_used:.1f}s), "
+                         f"scaled linearly to all columns"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64" if head == "fp32_simt" else f"c64 ({head})", "data": "synthetic",
+        "config": {"workload": "precision: 96^3 voxels (2 mm), 8-loop coil, 1024 segments, 298.2 MHz, "
+                               "HOSVD tol 1e-6, complex64 Tucker storage, p=16",
+                   "path": head, "M": inf.M, "max_rank": inf.max_rank, "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{ws}"},
+        "rel_err": {"y": results[head]["err_y"], "psi": results[head]["err_psi"], "vs": "FP64 oracle, sampled outputs"},
+        "paths": {n: {"fwd_ms": v["t_fwd_ms"], "adj_ms": v["t_adj_ms"], "err_y": v["err_y"], "err_psi": v["err_psi"],
+                      "tflops": F / ((v["t_fwd_ms"] + v["t_adj_ms"]) * 1e-3) / 1e12} for n, v in results.items()},
+        "e2e": {"value": ws * F / (e2e_ms * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "setup_s": t_build,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import greens, products, tucker
+    from paper_2103_06393_gb300 import inputs
+
+    w = inputs.workload(WORKLOAD)
+    g, s = w.grid, w.segments
+    p = w.p
+    # the reference arm runs the FP64 oracle on a bounded sample of columns per step
+    ncols = 4
+    X = inputs.cn01((s.m, p), seed=0)
+    Phi = inputs.cn01((3 * g.nv, p), seed=1)
+    Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(ncols))
+    tens = tucker.compress_columns(Z, g.shape, 3, w.tol)
+    ranks = np.array([[U.shape[1] for U in t[1]] for tj in tens for t in tj])
+    F_sample = 2.0 * products.flops(ranks, g.shape, 3, ncols, p)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        products.matvec(tens, g.shape, X[:ncols])
+        products.rmatvec(tens, g.shape, Phi)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    dt = float(np.mean(times))
+    value = F_sample / dt / 1e12
+    ms = 1e3 * dt * s.m / ncols   # the full step, extrapolated linearly in the columns
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "precision: 96^3 voxels (2 mm), 8-loop coil, 1024 segments, 298.2 MHz, "
+                               "HOSVD tol 1e-6, p=16", "path": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{ncols} of {s.m} columns per step, scaled linearly"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zbc", choices=["zbc", "reference"])
+    ap.add_argument("--prec", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_zbc(args)
+
+
+if __name__ == "__main__":
+    main()

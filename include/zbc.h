@@ -101,6 +101,10 @@ const char* zbc_last_error(void);
 /* Library version string. */
 const char* zbc_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all entry points).
+ * Lets a caller count the launches inside a timed region. */
+int64_t zbc_kernel_launches(void);
+
 /*
  * vsie_assemble_columns -- columns of the coupling matrix (Sec. III.A; Eq. n6, Eq. nNt).
  *   Z[(k,v), e] = h^3 len_e [ (I + grad grad / k0^2) g(r_v - c_e) t_e ]_k,

@@ -1,6 +1,7 @@
 // Handle lifetime, host import/export, checkpoints and error reporting of the C ABI.
 #include <cstdarg>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 
 #include "zbc_internal.cuh"
@@ -133,6 +134,9 @@ int handle_append(Handle* h, const std::vector<int32_t>& ranks, const float2* d_
   return finish_desc(h);
 }
 
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -151,6 +155,8 @@ using namespace zbc;
 extern "C" const char* zbc_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* zbc_version(void) { return "zbc 0.1 (sm_103a)"; }
+
+extern "C" int64_t zbc_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 extern "C" int zbc_free(zbc_handle* h) {
   delete h;

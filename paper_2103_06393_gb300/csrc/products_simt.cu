@@ -298,12 +298,14 @@ int aca_pre(const Handle& h, const float2* X, int64_t ldx, int p, float2* Xp, cu
   const int64_t n = (int64_t)h.M * p;
   small_gemm_kernel<<<ceil_div(n, 256), 256, 0, st>>>(h.d_v, h.m, h.M, 1, X, ldx, p, Xp, h.M);
   ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
   return ZBC_OK;
 }
 int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ldpsi, cudaStream_t st) {
   const int64_t n = (int64_t)h.m * p;
   small_gemm_kernel<<<ceil_div(n, 256), 256, 0, st>>>(h.d_v, h.m, h.M, 0, Psip, h.M, p, Psi, ldpsi);
   ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
   return ZBC_OK;
 }
 
@@ -331,6 +333,7 @@ static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, f
   dim3 grid(tg.t1 * tg.t2 * tg.t3, h.q, ceil_div(p, PS));
   matvec_simt_kernel<PS><<<grid, 256, sm, st>>>(h.d_pool, h.d_desc, tg, h.q, h.M, R, X, ldx, p, Y, ldy);
   ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
   return ZBC_OK;
 }
 
@@ -361,6 +364,7 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   ZBC_TRY_CUDA(cudaGetLastError());
   reduce_partials_kernel<<<ceil_div((int64_t)h.M * p, 256), 256, 0, st>>>(partial, G * h.q, h.M, p, out, ldo);
   ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch(2);
   return ZBC_OK;
 }
 

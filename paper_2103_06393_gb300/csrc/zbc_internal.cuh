@@ -119,6 +119,9 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 int sm_count();
 
+// number of kernels this library has launched (all entry points), for launch accounting
+void count_launch(int n = 1);
+
 }  // namespace zbc
 
 struct zbc_handle {

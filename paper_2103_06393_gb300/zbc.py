@@ -63,6 +63,7 @@ def lib():
         sig = {
             "zbc_last_error": ([], C.c_char_p),
             "zbc_version": ([], C.c_char_p),
+            "zbc_kernel_launches": ([], C.c_int64),
             "vsie_assemble_columns": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, vp, i64, i32, vp], i32),
             "tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, i32, C.POINTER(vp),
                                  C.POINTER(zbc_compress_stats), vp], i32),
@@ -82,6 +83,10 @@ def lib():
             f.restype = res
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    return int(lib().zbc_kernel_launches())
 
 
 def _check(status):
