@@ -187,6 +187,16 @@ int zbc_create_from_host(const zbc_grid* g, int q, int M, int m, const int32_t* 
  * pool_elems = pool_bytes/8); v_host: complex64[m*M] or NULL.  Synchronises the device. */
 int zbc_export_host(const zbc_handle* h, int32_t* ranks_host, void* pool_host, void* v_host);
 
+/*
+ * zbc_tc_selftest -- diagnostic of the tensor-core operand path (no counterpart in the paper):
+ * D (128 x N, row-major) = A (128 x K, row-major) * B (N x K, row-major)^T computed with one
+ * chain of tcgen05.mma through the shared-memory layout and descriptors of the product
+ * kernels, operands rounded to fmt (0 = fp16, 1 = bf16, 2 = tf32), FP32 accumulation.
+ * Host pointers; N in {16, 32, 48, 64}; K a multiple of 16 (fp16/bf16) or 8 (tf32), <= 64.
+ * Synchronises the device.  Returns ZBC_ETIMEOUT if the MMA completion wait gave up.
+ */
+int zbc_tc_selftest(const float* A_host, const float* B_host, float* D_host, int N, int K, int fmt);
+
 /* Checkpoint: flat little-endian file "ZBC1" + header + ranks + pool + V.  zbc_load creates
  * a new handle on the current device. */
 int zbc_save(const zbc_handle* h, const char* path);

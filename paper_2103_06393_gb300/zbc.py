@@ -76,6 +76,7 @@ def lib():
             "zbc_export_host": ([vp, vp, vp, vp], i32),
             "zbc_save": ([vp, C.c_char_p], i32),
             "zbc_load": ([C.c_char_p, C.POINTER(vp)], i32),
+            "zbc_tc_selftest": ([vp, vp, vp, i32, i32, i32], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -222,6 +223,16 @@ def zbc_create_from_host(grid, q, tensors, V=None) -> Handle:
                                       pool.ctypes.data_as(C.c_void_p), pool.size,
                                       vcol.ctypes.data_as(C.c_void_p) if vcol is not None else None, C.byref(h)))
     return Handle(h)
+
+
+def zbc_tc_selftest(A: np.ndarray, B: np.ndarray, fmt: int) -> np.ndarray:
+    """D = A B^T through one tcgen05 MMA chain (A 128 x K, B N x K float32)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    D = np.zeros((128, B.shape[0]), dtype=np.float32)
+    _check(lib().zbc_tc_selftest(A.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p),
+                                 D.ctypes.data_as(C.c_void_p), B.shape[0], A.shape[1], fmt))
+    return D
 
 
 def zbc_load(path: str) -> Handle:
