@@ -12,7 +12,7 @@
 namespace zbc {
 
 // ---------------------------------------------------------------------------------------------
-// Algorithm 1
+// Algorithm 1: one task (32 i1 x kUQ u) per warp
 // ---------------------------------------------------------------------------------------------
 template <int PS>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -21,15 +21,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                        int64_t ldy) {
   extern __shared__ __align__(16) unsigned char smem[];
   ChunkSmem cs;
-  float2* xs = (float2*)cs.carve(smem, R, g.NU);  // [kChunk][PS]
+  float2* xs = (float2*)cs.carve(smem, R, g.NUp);  // [kChunk][PS]
   const int k = blockIdx.y;
   const int s0 = blockIdx.z * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int i1_0, i2_0, i3;
   g.tile(blockIdx.x, i1_0, i2_0, i3);
-  float2 acc[kMaxLG][PS];
+  const bool active = warp < g.ntask;
+  int i1 = 0, u0 = 0;
+  bool ok = false;
+  if (active) g.task(i1_0, warp, lane, i1, u0, ok);
+  float2 acc[kUQ][PS];
 #pragma unroll
-  for (int l = 0; l < kMaxLG; ++l)
+  for (int l = 0; l < kUQ; ++l)
 #pragma unroll
     for (int i = 0; i < PS; ++i) acc[l][i] = make_float2(0.f, 0.f);
   for (int j0 = 0; j0 < M; j0 += kChunk) {
@@ -39,31 +43,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       xs[e] = (s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
     }
     chunk_pw(pool, desc, g, q, k, j0, jc, R, i2_0, i3, cs);
-    for (int jj = 0; jj < jc; ++jj) {
-      const TensorDesc d = cs.jd[jj];
-      const float2* U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3;
-      const float2* Wj = cs.W + (size_t)jj * R * g.NU;
+    if (active) {
+      for (int jj = 0; jj < jc; ++jj) {
+        const TensorDesc d = cs.jd[jj];
+        float2 z[kUQ];
+        last_mode4(pool + d.off + (int64_t)d.r1 * d.r2 * d.r3, g.n1, d.r1, i1, ok,
+                   cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
 #pragma unroll
-      for (int l = 0; l < kMaxLG; ++l) {
-        const int gi = warp + 8 * l;
-        if (gi >= g.nlg) break;
-        int i1, u;
-        const bool ok = g.voxel(i1_0, i2_0, gi, lane, i1, u);
-        const float2 z = ok ? last_mode(U1, g.n1, d.r1, i1, Wj, R, g.NU, u) : make_float2(0.f, 0.f);
+        for (int i = 0; i < PS; ++i) {
+          const float2 x = xs[jj * PS + i];
 #pragma unroll
-        for (int i = 0; i < PS; ++i) acc[l][i] = cfma(z, xs[jj * PS + i], acc[l][i]);
+          for (int l = 0; l < kUQ; ++l) acc[l][i] = cfma(z[l], x, acc[l][i]);
+        }
       }
     }
     __syncthreads();
   }
+  if (!active || !ok) return;
   const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
 #pragma unroll
-  for (int l = 0; l < kMaxLG; ++l) {
-    const int gi = warp + 8 * l;
-    if (gi >= g.nlg) break;
-    int i1, u;
-    if (!g.voxel(i1_0, i2_0, gi, lane, i1, u)) continue;
-    const int64_t v = i1 + (int64_t)g.n1 * ((i2_0 + u) + (int64_t)g.n2 * i3);
+  for (int l = 0; l < kUQ; ++l) {
+    const int i2 = i2_0 + u0 + l;
+    if (u0 + l >= g.NU || i2 >= g.n2) continue;
+    const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
     float2* y = Y + k * nv + v;
 #pragma unroll
     for (int i = 0; i < PS; ++i)
@@ -114,51 +116,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int SH = 5 - Log2<NV>::v;
   extern __shared__ __align__(16) unsigned char smem[];
   ChunkSmem cs;
-  float* red = (float*)cs.carve(smem, R, g.NU);  // [kChunk][8][NV]
-  float* pacc = red + kChunk * 8 * NV;             // [MJ][NV]
+  float* red = (float*)cs.carve(smem, R, g.NUp);  // [kChunk][8][NV]
+  float* pacc = red + kChunk * 8 * NV;              // [MJ][NV]
   const int k = blockIdx.y % q;
   const int jb0 = (blockIdx.y / q) * MJ;
   const int jb1 = min(M, jb0 + MJ);
   const int s0 = blockIdx.z * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
+  const bool active = warp < g.ntask;
   for (int e = threadIdx.x; e < (jb1 - jb0) * NV; e += blockDim.x) pacc[e] = 0.f;
   for (int t = blockIdx.x; t < g.ntiles(); t += gridDim.x) {
     int i1_0, i2_0, i3;
     g.tile(t, i1_0, i2_0, i3);
-    float2 ph[kMaxLG][PS];
+    int i1 = 0, u0 = 0;
+    bool ok = false;
+    if (active) g.task(i1_0, warp, lane, i1, u0, ok);
+    float2 ph[kUQ][PS];
 #pragma unroll
-    for (int l = 0; l < kMaxLG; ++l) {
-      const int gi = warp + 8 * l;
-      int i1 = 0, u = 0;
-      const bool ok = gi < g.nlg && g.voxel(i1_0, i2_0, gi, lane, i1, u);
-      const int64_t v = i1 + (int64_t)g.n1 * ((i2_0 + u) + (int64_t)g.n2 * i3);
+    for (int l = 0; l < kUQ; ++l) {
+      const int i2 = i2_0 + u0 + l;
+      const bool okl = ok && (u0 + l) < g.NU && i2 < g.n2;
+      const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
 #pragma unroll
       for (int i = 0; i < PS; ++i)
-        ph[l][i] = (ok && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
+        ph[l][i] = (okl && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
     }
     for (int j0 = jb0; j0 < jb1; j0 += kChunk) {
       const int jc = min(kChunk, jb1 - j0);
       chunk_pw(pool, desc, g, q, k, j0, jc, R, i2_0, i3, cs);
       for (int jj = 0; jj < jc; ++jj) {
         const TensorDesc d = cs.jd[jj];
-        const float2* U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3;
-        const float2* Wj = cs.W + (size_t)jj * R * g.NU;
+        float2 z[kUQ];
+        last_mode4(pool + d.off + (int64_t)d.r1 * d.r2 * d.r3, g.n1, d.r1, i1, ok && active,
+                   cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
         float vals[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) vals[i] = 0.f;
+        for (int i = 0; i < PS; ++i) {
+          float re = 0.f, im = 0.f;
 #pragma unroll
-        for (int l = 0; l < kMaxLG; ++l) {
-          const int gi = warp + 8 * l;
-          if (gi >= g.nlg) break;
-          int i1, u;
-          const bool ok = g.voxel(i1_0, i2_0, gi, lane, i1, u);
-          const float2 z = ok ? last_mode(U1, g.n1, d.r1, i1, Wj, R, g.NU, u) : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int i = 0; i < PS; ++i) {
-            vals[2 * i] = fmaf(z.x, ph[l][i].x, fmaf(z.y, ph[l][i].y, vals[2 * i]));
-            vals[2 * i + 1] = fmaf(z.x, ph[l][i].y, fmaf(-z.y, ph[l][i].x, vals[2 * i + 1]));
+          for (int l = 0; l < kUQ; ++l) {
+            re = fmaf(z[l].x, ph[l][i].x, fmaf(z[l].y, ph[l][i].y, re));
+            im = fmaf(z[l].x, ph[l][i].y, fmaf(-z[l].y, ph[l][i].x, im));
           }
+          vals[2 * i] = re;
+          vals[2 * i + 1] = im;
         }
         const float r = warp_reduce_scatter<NV>(vals, lane);
         if ((lane & ((1 << SH) - 1)) == 0) red[(jj * 8 + warp) * NV + (lane >> SH)] = r;
@@ -238,9 +240,9 @@ int reduce_partials(const float2* partial, int ng, int M, int p, float2* out, in
 
 template <int PS>
 static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
-  Geo g = make_geo(h.n1, h.n2, h.n3);
+  Geo g = make_geo(h.n1, h.n2, h.n3, 8);
   const int R = std::max(h.max_rank, 1);
-  const size_t sm = ChunkSmem::bytes(R, g.NU) + sizeof(float2) * kChunk * PS;
+  const size_t sm = ChunkSmem::bytes(R, g.NUp) + sizeof(float2) * kChunk * PS;
   static bool attr_set = false;
   if (!attr_set) {
     ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
@@ -257,10 +259,10 @@ static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, f
 template <int PS>
 static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
                           cudaStream_t st) {
-  Geo g = make_geo(h.n1, h.n2, h.n3);
+  Geo g = make_geo(h.n1, h.n2, h.n3, 8);
   const int R = std::max(h.max_rank, 1);
   const int NV = 2 * PS;
-  const size_t base = ChunkSmem::bytes(R, g.NU) + sizeof(float) * kChunk * 8 * NV;
+  const size_t base = ChunkSmem::bytes(R, g.NUp) + sizeof(float) * kChunk * 8 * NV;
   // j-block so that the per-CTA accumulator stays within the shared-memory budget
   const size_t budget = 220 * 1024 - base;
   const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
