@@ -47,6 +47,7 @@ Handle::~Handle() {
   if (d_desc) cudaFree(d_desc);
   if (d_v) cudaFree(d_v);
   if (tc) tc_release(tc);
+  if (cache) cache_release(cache);
 }
 
 int Handle::upload() {
@@ -130,6 +131,10 @@ int handle_append(Handle* h, const std::vector<int32_t>& ranks, const float2* d_
   if (h->tc) {
     tc_release(h->tc);
     h->tc = nullptr;
+  }
+  if (h->cache) {
+    cache_release(h->cache);
+    h->cache = nullptr;
   }
   return finish_desc(h);
 }

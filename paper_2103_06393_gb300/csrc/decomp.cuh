@@ -1,13 +1,14 @@
-// Chunked decompression front end shared by the product kernels (Sec. III.B, Eq. Tucker).
+// Decompression front end shared by the product kernels (Sec. III.B, Eq. Tucker).
 //
-// A CTA owns a voxel tile of B1 (i1) x NU (i2) voxels at one i3 and walks the stored
-// columns j in chunks of kChunk.  For every column of a chunk it forms, in shared memory,
-//   P_j[a][b] = sum_c G_j[a,b,c] U3_j[i3,c]          (core x3 one factor row)
-//   W_j[a][u] = sum_b P_j[a][b] U2_j[i2_0+u, b]       (x2 the tile's U2 rows)
-// so that the last mode product Z[i1,u,j] = sum_a U1_j[i1,a] W_j[a][u] costs r1 complex MACs
-// per voxel and column; the core contraction is amortised over the whole B1 x NU tile.
-// Work is split into tasks: a task is 32 consecutive i1 (one per lane) times kUQ consecutive u,
-// so each U1 row a thread loads serves kUQ voxels.
+// Z^{kj} = G x1 U1 x2 U2 x3 U3.  The partial product W_j = G_j x2 U2_j x3 U3_j (r1 x n2 x n3)
+// does not depend on the right-hand sides, so a handle keeps it (and a row-major copy of
+// U1_j) in a device cache built once, on the first product call (decomp_cache.cu).  A product
+// CTA then owns a voxel tile of B1 (i1) x NU (i2) voxels at one i3 and walks the stored
+// columns in chunks of kChunk: it stages the chunk's W blocks in shared memory (prefetched one
+// chunk ahead in registers) and forms the last mode product
+//   Z[i1, u, j] = sum_a U1_j[i1, a] W_j[a, i2_0 + u, i3]
+// on CUDA cores.  A task is 32 consecutive i1 (one per lane) times kUQ consecutive u, so each
+// U1 row a thread loads serves kUQ voxels.
 #pragma once
 
 #include "zbc_internal.cuh"
@@ -17,6 +18,15 @@ namespace zbc {
 constexpr int kChunk = 8;      // columns per chunk
 constexpr int kThreads = 256;  // threads per CTA
 constexpr int kUQ = 4;         // u values per task
+constexpr int kRmax = 32;      // largest rank r1 the product kernels accept
+constexpr int kWPre = 8;       // W values each thread prefetches per chunk (kChunk*kRmax*NUp/kThreads max)
+
+// per-tensor view of the decompression cache
+struct CacheDesc {
+  int64_t woff;   // W: [i3][i2][a] complex64, r1 per (i2, i3)
+  int64_t uoff;   // U1 row-major: [i1][a], row stride r1p (r1 rounded up to 2)
+  int r1, r1p;
+};
 
 struct Geo {
   int n1, n2, n3;
@@ -30,19 +40,17 @@ struct Geo {
     i2_0 = ((t / nb1) % nb2) * NU;
     i3 = t / (nb1 * nb2);
   }
-  // task tk, lane l -> i1 and first u; ok_i1 false for padding lanes
   __device__ __forceinline__ void task(int i1_0, int tk, int l, int& i1, int& u0, bool& ok_i1) const {
     i1 = i1_0 + 32 * (tk % nb32) + l;
     u0 = (tk / nb32) * kUQ;
     ok_i1 = i1 < n1 && (i1 - i1_0) < B1;
   }
-  // accumulator row of (task, lane, q) -- rows are grouped by 32 lanes
   __device__ __forceinline__ static int row(int tk, int q, int l) { return (tk * kUQ + q) * 32 + l; }
 };
 
-// NU chosen so that the tile has at most max_tasks tasks (and, for the tensor-core kernels,
-// the accumulator rows ntask * kUQ * 32 stay within max_rows).
-inline Geo make_geo(int n1, int n2, int n3, int max_tasks, int max_rows = 1 << 30) {
+// R = largest r1 of the handle (rounded up to 2): the chunk's W blocks (kChunk x R x NUp) must
+// fit the register prefetch (kWPre values per thread).
+inline Geo make_geo(int n1, int n2, int n3, int R, int max_tasks, int max_rows = 1 << 30) {
   Geo g;
   g.n1 = n1;
   g.n2 = n2;
@@ -53,6 +61,8 @@ inline Geo make_geo(int n1, int n2, int n3, int max_tasks, int max_rows = 1 << 3
   if (tasks * kUQ * 32 > max_rows) tasks = max_rows / (kUQ * 32);
   int nq = tasks / g.nb32;
   if (nq < 1) nq = 1;
+  const int nq_pre = (kWPre * kThreads) / (kChunk * R * kUQ);
+  if (nq > nq_pre) nq = nq_pre < 1 ? 1 : nq_pre;
   int nu = nq * kUQ;
   const int n2r = (n2 + kUQ - 1) / kUQ * kUQ;
   if (nu > n2r) nu = n2r;
@@ -64,75 +74,94 @@ inline Geo make_geo(int n1, int n2, int n3, int max_tasks, int max_rows = 1 << 3
   return g;
 }
 
+// shared memory of the front end: W[jj][a][NUp] (a < R) for one chunk, and the chunk's cache
+// entries
 struct ChunkSmem {
-  float2* P;        // [kChunk][R*R]
-  float2* W;        // [kChunk][R][NUp]
-  TensorDesc* jd;   // [kChunk]
+  float2* W;
+  CacheDesc* cd;
   static size_t bytes(int R, int NUp) {
-    return sizeof(float2) * ((size_t)kChunk * R * R + (size_t)kChunk * R * NUp) + sizeof(TensorDesc) * kChunk;
+    return sizeof(float2) * (size_t)kChunk * R * NUp + sizeof(CacheDesc) * kChunk;
   }
   __device__ __forceinline__ unsigned char* carve(unsigned char* base, int R, int NUp) {
-    P = (float2*)base;
-    W = P + (size_t)kChunk * R * R;
-    jd = (TensorDesc*)(W + (size_t)kChunk * R * NUp);
-    return (unsigned char*)(jd + kChunk);
+    W = (float2*)base;
+    cd = (CacheDesc*)(W + (size_t)kChunk * R * NUp);
+    return (unsigned char*)(cd + kChunk);
   }
 };
 
-// Steps P and W for columns j0 .. j0+jc-1 of component k (jc <= kChunk).  Ends with the W
-// values visible to all threads (two __syncthreads).
-__device__ __forceinline__ void chunk_pw(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc,
-                                         const Geo& g, int q, int k, int j0, int jc, int R, int i2_0, int i3,
-                                         const ChunkSmem& s) {
-  if (threadIdx.x < jc) s.jd[threadIdx.x] = desc[(int64_t)(j0 + threadIdx.x) * q + k];
-  __syncthreads();
-  const int RR = R * R;
-  for (int o = threadIdx.x; o < jc * RR; o += blockDim.x) {
-    const int jj = o / RR, ab = o % RR;
-    const TensorDesc d = s.jd[jj];
-    const int a = ab % R, b = ab / R;
-    if (a >= d.r1 || b >= d.r2) continue;
-    const float2* G = pool + d.off;
-    const float2* U3 = G + (int64_t)d.r1 * d.r2 * d.r3 + (int64_t)g.n1 * d.r1 + (int64_t)g.n2 * d.r2;
-    float2 acc = make_float2(0.f, 0.f);
-    const int64_t st = (int64_t)d.r1 * d.r2;
-    for (int c = 0; c < d.r3; ++c) acc = cfma(__ldg(G + a + d.r1 * b + st * c), __ldg(U3 + i3 + (int64_t)g.n3 * c), acc);
-    s.P[jj * RR + a * R + b] = acc;
-  }
-  __syncthreads();
-  const int RN = R * g.NUp;
-  for (int o = threadIdx.x; o < jc * RN; o += blockDim.x) {
-    const int jj = o / RN, rem = o % RN;
-    const int u = rem % g.NUp, a = rem / g.NUp;
-    const TensorDesc d = s.jd[jj];
-    float2 acc = make_float2(0.f, 0.f);
-    if (a < d.r1 && u < g.NU && i2_0 + u < g.n2) {
-      const float2* U2 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3 + (int64_t)g.n1 * d.r1;
-      for (int b = 0; b < d.r2; ++b) acc = cfma(s.P[jj * RR + a * R + b], __ldg(U2 + (i2_0 + u) + (int64_t)g.n2 * b), acc);
+// Register prefetch of one chunk's W blocks: element e = (jj, a, u) of W[jj][a][NUp].
+// Loaded one chunk ahead so the global-memory latency overlaps the current chunk's work.
+struct WPrefetch {
+  float2 v[kWPre];
+  CacheDesc cd;  // cache entry of column jj = threadIdx.x (threads < kChunk)
+  __device__ __forceinline__ void load(const float2* __restrict__ wc, const CacheDesc* __restrict__ cdesc,
+                                       const Geo& g, int R, int q, int k, int j0, int jc, int i2_0, int i3) {
+    if (threadIdx.x < jc) cd = cdesc[(int64_t)(j0 + threadIdx.x) * q + k];
+    const int per = R * g.NUp;
+#pragma unroll
+    for (int i = 0; i < kWPre; ++i) {
+      const int e = threadIdx.x + i * kThreads;
+      float2 x = make_float2(0.f, 0.f);
+      if (e < kChunk * per) {
+        const int jj = e / per, rem = e % per;
+        const int a = rem / g.NUp, u = rem % g.NUp;
+        if (jj < jc && u < g.NU && i2_0 + u < g.n2) {
+          const CacheDesc d = cdesc[(int64_t)(j0 + jj) * q + k];
+          if (a < d.r1) x = __ldg(wc + d.woff + ((int64_t)i3 * g.n2 + i2_0 + u) * d.r1 + a);
+        }
+      }
+      v[i] = x;
     }
-    s.W[(jj * R + a) * g.NUp + u] = acc;
   }
-  __syncthreads();
-}
+  __device__ __forceinline__ void store(const ChunkSmem& s, const Geo& g, int R, int jc) const {
+    const int per = R * g.NUp;
+#pragma unroll
+    for (int i = 0; i < kWPre; ++i) {
+      const int e = threadIdx.x + i * kThreads;
+      if (e < kChunk * per) s.W[e] = v[i];
+    }
+    if (threadIdx.x < jc) s.cd[threadIdx.x] = cd;
+  }
+};
 
 // Last mode product of one column for kUQ voxels sharing i1:
-//   z[q] = sum_a U1[i1, a] W[a][u0 + q]
-__device__ __forceinline__ void last_mode4(const float2* __restrict__ U1, int n1, int r1, int i1, bool ok,
-                                           const float2* Wj, int NUp, int u0, float2 (&z)[kUQ]) {
+//   z[l] = sum_a U1_j[i1, a] W_j[a][u0 + l]
+// U1 row loaded as float4 pairs from the row-major cache (all loads issued before use).
+__device__ __forceinline__ void last_mode4(const float2* __restrict__ u1row, int r1, bool ok, const float2* Wj,
+                                           int NUp, int u0, float2 (&z)[kUQ]) {
 #pragma unroll
-  for (int qq = 0; qq < kUQ; ++qq) z[qq] = make_float2(0.f, 0.f);
+  for (int l = 0; l < kUQ; ++l) z[l] = make_float2(0.f, 0.f);
   if (!ok) return;
+  float4 ur[kRmax / 2];
+  const float4* src = reinterpret_cast<const float4*>(u1row);
+#pragma unroll
+  for (int i = 0; i < kRmax / 2; ++i)
+    if (2 * i < r1) ur[i] = __ldg(src + i);
   const float4* w4 = reinterpret_cast<const float4*>(Wj + u0);
   const int stride4 = NUp / 2;
-#pragma unroll 4
-  for (int a = 0; a < r1; ++a) {
-    const float2 x = __ldg(U1 + i1 + (int64_t)n1 * a);
-    const float4 wa = w4[a * stride4], wb = w4[a * stride4 + 1];
-    z[0] = cfma(x, make_float2(wa.x, wa.y), z[0]);
-    z[1] = cfma(x, make_float2(wa.z, wa.w), z[1]);
-    z[2] = cfma(x, make_float2(wb.x, wb.y), z[2]);
-    z[3] = cfma(x, make_float2(wb.z, wb.w), z[3]);
+#pragma unroll
+  for (int i = 0; i < kRmax / 2; ++i) {
+    if (2 * i >= r1) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = 2 * i + h;
+      if (a >= r1) break;
+      const float2 x = h == 0 ? make_float2(ur[i].x, ur[i].y) : make_float2(ur[i].z, ur[i].w);
+      const float4 wa = w4[a * stride4], wb = w4[a * stride4 + 1];
+      z[0] = cfma(x, make_float2(wa.x, wa.y), z[0]);
+      z[1] = cfma(x, make_float2(wa.z, wa.w), z[1]);
+      z[2] = cfma(x, make_float2(wb.x, wb.y), z[2]);
+      z[3] = cfma(x, make_float2(wb.z, wb.w), z[3]);
+    }
   }
 }
+
+// the decompression cache of a handle (built by build_decomp_cache in decomp_cache.cu)
+struct DecompCache {
+  float2* data = nullptr;   // W blocks and U1 row-major copies
+  CacheDesc* d_desc = nullptr;
+  int64_t elems = 0;
+};
+int build_decomp_cache(Handle& h, cudaStream_t st);
 
 }  // namespace zbc

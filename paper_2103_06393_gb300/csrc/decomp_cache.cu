@@ -1,0 +1,112 @@
+// Decompression cache of a handle: per tensor (column j, component k)
+//   W_j[i3][i2][a] = sum_{b,c} G_j[a,b,c] U2_j[i2,b] U3_j[i3,c]     (= G x2 U2 x3 U3, Eq. Tucker)
+//   U1_j row-major [i1][a] with row stride r1 rounded up to 2 (16-byte aligned rows)
+// Both depend only on the compressed data, so they are computed once (first product call) and
+// reused by every product; the last mode product with U1 stays in the product kernels.
+// Size: sum over tensors of (n2 n3 r1 + n1 r1p) complex64.
+#include <algorithm>
+
+#include "decomp.cuh"
+
+namespace zbc {
+
+void cache_release(DecompCache* c) {
+  if (!c) return;
+  if (c->data) cudaFree(c->data);
+  if (c->d_desc) cudaFree(c->d_desc);
+  delete c;
+}
+
+// one CTA per (i3, tensor): P[a][b] = sum_c G[a,b,c] U3[i3,c]; W[i3][i2][a] = sum_b P[a][b] U2[i2,b]
+__global__ void __launch_bounds__(256) build_w_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc,
+                                                      const CacheDesc* __restrict__ cdesc, int n1, int n2, int n3,
+                                                      float2* __restrict__ cache) {
+  extern __shared__ float2 Ps[];  // r1 * r2
+  const int i3 = blockIdx.x, t = blockIdx.y;
+  const TensorDesc d = desc[t];
+  const CacheDesc cd = cdesc[t];
+  const float2* G = pool + d.off;
+  const float2* U2 = G + (int64_t)d.r1 * d.r2 * d.r3 + (int64_t)n1 * d.r1;
+  const float2* U3 = U2 + (int64_t)n2 * d.r2;
+  const int64_t st = (int64_t)d.r1 * d.r2;
+  for (int o = threadIdx.x; o < d.r1 * d.r2; o += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < d.r3; ++c) acc = cfma(G[o + st * c], U3[i3 + (int64_t)n3 * c], acc);
+    Ps[o] = acc;  // o = a + r1 * b
+  }
+  __syncthreads();
+  float2* W = cache + cd.woff + (int64_t)i3 * n2 * d.r1;
+  for (int o = threadIdx.x; o < n2 * d.r1; o += blockDim.x) {
+    const int a = o % d.r1, i2 = o / d.r1;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < d.r2; ++b) acc = cfma(Ps[a + d.r1 * b], U2[i2 + (int64_t)n2 * b], acc);
+    W[o] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) build_u1_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc,
+                                                       const CacheDesc* __restrict__ cdesc, int n1,
+                                                       float2* __restrict__ cache) {
+  const int t = blockIdx.y;
+  const TensorDesc d = desc[t];
+  const CacheDesc cd = cdesc[t];
+  const float2* U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n1 * cd.r1p; o += gridDim.x * blockDim.x) {
+    const int a = o % cd.r1p, i1 = o / cd.r1p;
+    cache[cd.uoff + o] = a < d.r1 ? U1[i1 + (int64_t)n1 * a] : make_float2(0.f, 0.f);
+  }
+}
+
+int build_decomp_cache(Handle& h, cudaStream_t st) {
+  if (h.cache) return ZBC_OK;
+  const int T = (int)h.desc.size();
+  std::vector<CacheDesc> cd(T);
+  int64_t off = 0;
+  int rmax = 0, r2max = 0;
+  for (int t = 0; t < T; ++t) {
+    const TensorDesc& d = h.desc[t];
+    cd[t].r1 = d.r1;
+    cd[t].r1p = (d.r1 + 1) / 2 * 2;
+    cd[t].woff = off;
+    off += (int64_t)h.n2 * h.n3 * d.r1;
+    off = (off + 1) / 2 * 2;
+    cd[t].uoff = off;
+    off += (int64_t)h.n1 * cd[t].r1p;
+    rmax = std::max(rmax, cd[t].r1p);
+    r2max = std::max(r2max, d.r1 * d.r2);
+  }
+  if (rmax > kRmax) {
+    set_error("product kernels support ranks r1 <= %d (handle has %d)", kRmax, rmax);
+    return ZBC_EINVAL;
+  }
+  auto* c = new DecompCache();
+  c->elems = off;
+  cudaError_t e = cudaMalloc(&c->data, sizeof(float2) * std::max<int64_t>(1, off));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_desc, sizeof(CacheDesc) * T);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_desc, cd.data(), sizeof(CacheDesc) * T, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cache_release(c);
+    set_error("decompression cache allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
+  }
+  const size_t sm = sizeof(float2) * r2max;
+  for (int t0 = 0; t0 < T; t0 += 65535) {
+    const int nt = std::min(65535, T - t0);
+    build_w_kernel<<<dim3(h.n3, nt), 256, sm, st>>>(h.d_pool, h.d_desc + t0, c->d_desc + t0, h.n1, h.n2, h.n3, c->data);
+    build_u1_kernel<<<dim3(ceil_div((int64_t)h.n1 * rmax, 256), nt), 256, 0, st>>>(h.d_pool, h.d_desc + t0, c->d_desc + t0,
+                                                                                h.n1, c->data);
+    count_launch(2);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cache_release(c);
+    set_error("decompression cache build failed: %s", cudaGetErrorString(e));
+    return ZBC_ECUDA;
+  }
+  h.cache = c;
+  h.cache_r = rmax;
+  return ZBC_OK;
+}
+
+}  // namespace zbc

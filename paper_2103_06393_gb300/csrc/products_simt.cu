@@ -16,7 +16,7 @@ namespace zbc {
 // ---------------------------------------------------------------------------------------------
 template <int PS>
 __global__ void __launch_bounds__(kThreads, 1)
-    matvec_simt_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc, Geo g, int q, int M,
+    matvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                        int R, const float2* __restrict__ X, int64_t ldx, int p, float2* __restrict__ Y,
                        int64_t ldy) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -36,19 +36,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int l = 0; l < kUQ; ++l)
 #pragma unroll
     for (int i = 0; i < PS; ++i) acc[l][i] = make_float2(0.f, 0.f);
+  WPrefetch pf;
+  pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3);
   for (int j0 = 0; j0 < M; j0 += kChunk) {
     const int jc = min(kChunk, M - j0);
     for (int e = threadIdx.x; e < jc * PS; e += blockDim.x) {
       const int jj = e / PS, i = e % PS;
       xs[e] = (s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
     }
-    chunk_pw(pool, desc, g, q, k, j0, jc, R, i2_0, i3, cs);
+    pf.store(cs, g, R, jc);
+    __syncthreads();
+    if (j0 + kChunk < M) pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3);
     if (active) {
       for (int jj = 0; jj < jc; ++jj) {
-        const TensorDesc d = cs.jd[jj];
+        const CacheDesc d = cs.cd[jj];
         float2 z[kUQ];
-        last_mode4(pool + d.off + (int64_t)d.r1 * d.r2 * d.r3, g.n1, d.r1, i1, ok,
-                   cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
+        last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok, cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
           const float2 x = xs[jj * PS + i];
@@ -109,7 +112,7 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
 // ---------------------------------------------------------------------------------------------
 template <int PS>
 __global__ void __launch_bounds__(kThreads, 1)
-    rmatvec_simt_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc, Geo g, int q, int M,
+    rmatvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                         int R, int MJ, const float2* __restrict__ Phi, int64_t ldphi, int p,
                         float2* __restrict__ partial) {
   constexpr int NV = 2 * PS;
@@ -142,14 +145,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = 0; i < PS; ++i)
         ph[l][i] = (okl && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
     }
+    WPrefetch pf;
+    pf.load(cache, cdesc, g, R, q, k, jb0, min(kChunk, jb1 - jb0), i2_0, i3);
     for (int j0 = jb0; j0 < jb1; j0 += kChunk) {
       const int jc = min(kChunk, jb1 - j0);
-      chunk_pw(pool, desc, g, q, k, j0, jc, R, i2_0, i3, cs);
+      pf.store(cs, g, R, jc);
+      __syncthreads();
+      if (j0 + kChunk < jb1) pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, jb1 - j0 - kChunk), i2_0, i3);
       for (int jj = 0; jj < jc; ++jj) {
-        const TensorDesc d = cs.jd[jj];
+        const CacheDesc d = cs.cd[jj];
         float2 z[kUQ];
-        last_mode4(pool + d.off + (int64_t)d.r1 * d.r2 * d.r3, g.n1, d.r1, i1, ok && active,
-                   cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
+        last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok && active, cs.W + (size_t)jj * R * g.NUp, g.NUp,
+                   u0, z);
         float vals[NV];
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
@@ -239,9 +246,10 @@ int reduce_partials(const float2* partial, int ng, int M, int p, float2* out, in
 }
 
 template <int PS>
-static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
-  Geo g = make_geo(h.n1, h.n2, h.n3, 8);
-  const int R = std::max(h.max_rank, 1);
+static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
+  ZBC_TRY(build_decomp_cache(h, st));
+  const int R = h.cache_r;
+  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
   const size_t sm = ChunkSmem::bytes(R, g.NUp) + sizeof(float2) * kChunk * PS;
   static bool attr_set = false;
   if (!attr_set) {
@@ -250,7 +258,8 @@ static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, f
   }
   ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT path", R);
   dim3 grid(g.ntiles(), h.q, ceil_div(p, PS));
-  matvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.d_pool, h.d_desc, g, h.q, h.M, R, X, ldx, p, Y, ldy);
+  matvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, X, ldx, p, Y,
+                                                     ldy);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;
@@ -259,8 +268,9 @@ static int launch_matvec(const Handle& h, const float2* X, int64_t ldx, int p, f
 template <int PS>
 static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
                           cudaStream_t st) {
-  Geo g = make_geo(h.n1, h.n2, h.n3, 8);
-  const int R = std::max(h.max_rank, 1);
+  ZBC_TRY(build_decomp_cache(h, st));
+  const int R = h.cache_r;
+  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
   const int NV = 2 * PS;
   const size_t base = ChunkSmem::bytes(R, g.NUp) + sizeof(float) * kChunk * 8 * NV;
   // j-block so that the per-CTA accumulator stays within the shared-memory budget
@@ -281,13 +291,14 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)G * h.q * h.M * p));
   float2* partial = (float2*)h.work_partial.ptr;
   dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.d_pool, h.d_desc, g, h.q, h.M, R, MJ, Phi, ldphi, p, partial);
+  rmatvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
+                                                      p, partial);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(partial, G * h.q, h.M, p, out, ldo, st);
 }
 
-int matvec_simt(const Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
+int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
   if (p == 1) return launch_matvec<1>(h, X, ldx, p, Y, ldy, st);
   if (p == 2) return launch_matvec<2>(h, X, ldx, p, Y, ldy, st);
   if (p <= 4) return launch_matvec<4>(h, X, ldx, p, Y, ldy, st);

@@ -98,7 +98,7 @@ struct TcLayout {
 
 template <int FMT, int P2>
 __global__ void __launch_bounds__(kThreads, 1)
-    matvec_tc_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc, Geo g, int q, int M,
+    matvec_tc_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                      int R, TcLayout L, const float2* __restrict__ X, int64_t ldx, int p, float2* __restrict__ Y,
                      int64_t ldy, int* __restrict__ err) {
   using F = Fmt<FMT>;
@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     s_valid = true;
   };
 
+  WPrefetch pf;
+  pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3);
   for (int c = 0; c < nchunks; ++c) {
     const int buf = c & 1;
     const int j0 = c * kChunk;
@@ -182,7 +184,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int jj = e / P, i = e % P;
       xs[e] = (jj < jc && s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
     }
-    chunk_pw(pool, desc, g, q, k, j0, jc, R, i2_0, i3, cs);
+    pf.store(cs, g, R, jc);
+    __syncthreads();
+    if (j0 + kChunk < M) pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3);
     // B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk
     {
       const int nk16 = 2 * kChunk / NF;
@@ -215,9 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int jj = 0; jj < kChunk; ++jj) {
         float2 zz[kUQ];
         if (jj < jc) {
-          const TensorDesc d = cs.jd[jj];
-          last_mode4(pool + d.off + (int64_t)d.r1 * d.r2 * d.r3, g.n1, d.r1, i1, ok, cs.W + (size_t)jj * R * g.NUp,
-                     g.NUp, u0, zz);
+          const CacheDesc d = cs.cd[jj];
+          last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok, cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, zz);
         } else {
 #pragma unroll
           for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
@@ -316,7 +319,8 @@ template <int FMT, int P2>
 static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
   using F = Fmt<FMT>;
   constexpr int P = P2 / 2;
-  const int R = std::max(h.max_rank, 1);
+  ZBC_TRY(build_decomp_cache(h, st));
+  const int R = h.cache_r;
   // rows limited by TMEM (D and S: 2 * nmt * P2 <= 512) and by two shared-memory A buffers;
   // the largest tile (most tasks) that fits both is taken.
   const int tmem_rows = 128 * std::max(1, 256 / P2);
@@ -326,7 +330,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
   size_t sm = 0;
   int tasks = 16;
   for (; tasks >= 1; --tasks) {
-    g = make_geo(h.n1, h.n2, h.n3, tasks, tmem_rows);
+    g = make_geo(h.n1, h.n2, h.n3, R, tasks, tmem_rows);
     L.NR = g.ntask * kUQ * 32;
     L.nmt = L.NR / 128;
     L.KBA = 2 * kChunk * F::esz / 16;
@@ -352,7 +356,8 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
   int* err = (int*)h.work_misc.ptr;
   ZBC_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
-  matvec_tc_kernel<FMT, P2><<<grid, kThreads, sm, st>>>(h.d_pool, h.d_desc, g, h.q, h.M, R, L, X, ldx, p, Y, ldy, err);
+  matvec_tc_kernel<FMT, P2><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, L, X, ldx, p,
+                                                        Y, ldy, err);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;

@@ -66,7 +66,9 @@ struct TensorDesc {
   float scale_log2;   // floor(log2 ||G||_F), used for the per-column scaling of the fp16 path
 };
 
-struct TcPack;  // tensor-core operand staging, built lazily (products_tc.cu)
+struct TcPack;       // tensor-core operand staging, built lazily (products_tc.cu)
+struct DecompCache;  // W = G x2 U2 x3 U3 and row-major U1 per tensor, built lazily (decomp_cache.cu)
+void cache_release(DecompCache* c);
 
 struct Handle {
   int n1 = 0, n2 = 0, n3 = 0, q = 0;
@@ -85,6 +87,8 @@ struct Handle {
   DevBuf work_x;         // X' = V^H X (ACA), scaled operands
   DevBuf work_misc;
   TcPack* tc = nullptr;
+  DecompCache* cache = nullptr;
+  int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
   ~Handle();
   int64_t nv() const { return (int64_t)n1 * n2 * n3; }
   int upload();          // copy desc to device (pool already on device)
