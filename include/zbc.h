@@ -138,6 +138,36 @@ int tucker_compress(const void* cols, int64_t ld, int ncols, const zbc_grid* g, 
                     zbc_dtype in_dt, double tol, zbc_tucker_method method,
                     zbc_handle** out, zbc_compress_stats* stats_host, zbc_stream stream);
 
+typedef struct {
+  int32_t rank;             /* r_c: columns of U and V */
+  int32_t converged;        /* 1 if the stopping test |x||y| <= tol sqrt(s) was met */
+  int32_t row_restarts;     /* all-zero residual rows skipped (masked voxels) */
+  int32_t max_tucker_rank;  /* largest Tucker rank of the compressed U */
+  double s2;                /* running estimate of ||U V^H||_F^2 */
+  double last_term;         /* |x||y| of the last appended column */
+  double max_tucker_err;    /* largest HOSVD error bound (relative) over the tensors of U */
+} zbc_aca_stats;
+
+/*
+ * aca_compress -- Z ~ U V^H by partially pivoted ACA (Sec. II.B.2), then U column-wise in
+ * Tucker form (Sec. III.A), or directly Algorithm 3 (Sec. III.C: U assembled compressed, rows
+ * of U by element-wise Tucker evaluation, residual columns by Algorithms 1 and 2).
+ *   Rows and columns of Z come from the same point-matched kernel as vsie_assemble_columns.
+ *   tol        : ACA stopping tolerance eps (|x||y| <= eps sqrt(s_k))
+ *   max_rank   : upper bound on r_c
+ *   mode       : ZBC_ACA_DENSE_U (dense U in HBM, complex128, compressed at the end) or
+ *                ZBC_ACA_ALG3 (U never dense; each new column compressed at tucker_tol)
+ *   tucker_tol : HOSVD tolerance for U's tensors; <= 0 selects 3*tol (Algorithm 3's choice)
+ *   out        : new handle with U (Tucker, r_c columns) and V (m x r_c) -- Z = U V^H
+ *   pivots_host: optional int32[2*max_rank]: (row, column) pivot pairs in order
+ * Pivots, norms and the stopping test are FP64.  Ties pick the lowest index; rows and columns
+ * already used are excluded; the start row is 0 and an all-zero residual row (masked voxel)
+ * moves to the next unused row.  Synchronises the stream every iteration.
+ */
+int aca_compress(const zbc_grid* g, const zbc_segments* s, double freq_hz, int q, double tol, int max_rank,
+                 zbc_aca_mode mode, double tucker_tol, zbc_handle** out, zbc_aca_stats* stats_host,
+                 int32_t* pivots_host, zbc_stream stream);
+
 /*
  * zbc_matvec -- Y = Z X (Algorithm 1, Sec. III.B).  With ACA storage (Z = U V^H) the library
  * first forms X' = V^H X (r_c x p) and runs Algorithm 1 on U (Sec. III.B, last paragraph).

@@ -50,6 +50,12 @@ class zbc_compress_stats(C.Structure):
                 ("max_rel_err", C.c_double)]
 
 
+class zbc_aca_stats(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("converged", C.c_int32), ("row_restarts", C.c_int32),
+                ("max_tucker_rank", C.c_int32), ("s2", C.c_double), ("last_term", C.c_double),
+                ("max_tucker_err", C.c_double)]
+
+
 _lib = None
 
 
@@ -77,6 +83,8 @@ def lib():
             "zbc_save": ([vp, C.c_char_p], i32),
             "zbc_load": ([C.c_char_p, C.POINTER(vp)], i32),
             "zbc_tc_selftest": ([vp, vp, vp, i32, i32, i32], i32),
+            "aca_compress": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, i32, dbl, i32, i32, dbl,
+                              C.POINTER(vp), C.POINTER(zbc_aca_stats), vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -278,6 +286,19 @@ def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle
     if append_to is not None:
         return append_to, st
     return Handle(h), st
+
+
+def aca_compress(grid, dsegs: DeviceSegments, freq_hz: float, tol: float, max_rank: int, mode=ACA_DENSE_U,
+                 tucker_tol: float = 0.0, q=3, stream=None):
+    """Returns (Handle with U (Tucker) and V, stats, pivots array (r_c, 2))."""
+    g = grid_struct(grid)
+    s = dsegs.struct()
+    h = C.c_void_p()
+    st = zbc_aca_stats()
+    piv = np.zeros(2 * max_rank, dtype=np.int32)
+    _check(lib().aca_compress(C.byref(g), C.byref(s), freq_hz, q, tol, max_rank, mode, tucker_tol, C.byref(h),
+                              C.byref(st), piv.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return Handle(h), st, piv[:2 * st.rank].reshape(-1, 2)
 
 
 def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):
