@@ -169,6 +169,63 @@ int aca_compress(const zbc_grid* g, const zbc_segments* s, double freq_hz, int q
                  int32_t* pivots_host, zbc_stream stream);
 
 /*
+ * tucker_compress_randomized -- column-wise Tucker compression by a fixed-width randomized range
+ * finder with an HOSVD fallback (no counterpart in the paper; Halko-Martinsson-Tropp range finder
+ * per mode, as in the randomized HOSVD of Minster-Saibaba-Kilmer).  Per tensor t = j*q + k and
+ * mode g: Y = A_(g) Omega_g[:, :w] (FP32 sketch), Q = orth(Y) (FP64 Householder),
+ * C = A x1 Q1^H x2 Q2^H x3 Q3^H, e^2 = ||A||^2 - ||C||^2 (FP64).  If e^2 > tol^2 ||A||^2 the
+ * tensor is recompressed by truncated HOSVD (counted in stats n_fallback); otherwise C is
+ * truncated by HOSVD with the remaining budget (tol^2||A||^2 - e^2)/3 per mode and U_g = Q_g W_g,
+ * so ||A - A~||_F <= tol ||A||_F either way.
+ *   widths_host : int32[3*ncols*q], width w for (tensor t, mode g) at 3t+g; clamped to
+ *                 [2, min(n_g, lmax, 64)] and made even (rounded up when room allows)
+ *   sketch1/2/3 : device complex64 Gaussian test matrices Omega_g, (N_g x lmax) column-major with
+ *                 N_1 = n2 n3 (unfolding column c = i2 + n2 i3), N_2 = n1 n3 (c = i1 + n1 i3),
+ *                 N_3 = n1 n2 (c = i1 + n1 i2); shared by all tensors
+ *   out         : as tucker_compress (new handle or append)
+ * Synchronises the stream.
+ */
+int tucker_compress_randomized(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
+                               double tol, const int32_t* widths_host, const void* sketch1, const void* sketch2,
+                               const void* sketch3, int lmax, zbc_handle** out, zbc_compress_stats* stats_host,
+                               zbc_stream stream);
+
+/*
+ * Rank-predictor MLP (no counterpart in the paper): 7 -> 64 -> 64 -> 64 -> 9 with ReLU, trained
+ * on the GPU on log Tucker ranks.  Inputs per column (row-major, float32): segment centre / 0.1 m
+ * (3), unit tangent (3), distance to the voxel box / 0.1 m (1).  Outputs: log(rank) of
+ * component k, mode g at index 3k + g.  Weights are FP32 master copies; forward and backward use
+ * the weights rounded to bf16 with FP32 arithmetic; loss = mean squared error over batch and
+ * outputs; Adam (beta1 0.9, beta2 0.999, eps 1e-8) with bias correction.
+ * Parameter packing (float32): W1 (64x7 row-major [out][in]), b1 (64), W2 (64x64), b2, W3 (64x64),
+ * b3, W4 (9x64), b4 (9) -- zbc_mlp_num_params() values.
+ */
+typedef struct zbc_mlp zbc_mlp;
+int zbc_mlp_num_params(void);
+int zbc_mlp_create(const float* params_host, int n_params, zbc_mlp** out);
+int zbc_mlp_free(zbc_mlp* model);
+/* master_host / bf16_host: optional float32[n_params] copies of the master and bf16-rounded weights */
+int zbc_mlp_get_params(const zbc_mlp* model, float* master_host, float* bf16_host);
+/* out (device, B x 9 row-major) = MLP(X (device, B x 7 row-major)) */
+int zbc_mlp_forward(const zbc_mlp* model, const float* X, int B, float* out, zbc_stream stream);
+/* grads (device, n_params) = d loss / d weights at the bf16 weights; loss (device scalar, optional).
+ * Deterministic: per-CTA partial sums reduced in a fixed order. */
+int zbc_mlp_backward(zbc_mlp* model, const float* X, const float* T, int B, float* grads, float* loss,
+                     zbc_stream stream);
+/* one Adam update of the master weights with gradients grads (device) */
+int zbc_mlp_adam_step(zbc_mlp* model, const float* grads, float lr, zbc_stream stream);
+/* steps x (backward + Adam) on the full batch; loss_hist (device, steps floats, optional) */
+int zbc_mlp_train(zbc_mlp* model, const float* X, const float* T, int B, int steps, float lr, float* loss_hist,
+                  zbc_stream stream);
+/*
+ * zbc_rank_widths -- widths for tucker_compress_randomized from the MLP: features (device,
+ * ncols x 7) -> predicted log ranks -> w = ceil(exp(pred)) + oversample, clamped to [2, n_g].
+ * widths_host: int32[9*ncols] in the (tensor t = 3j + k, mode g) -> 3t + g order.  Synchronises.
+ */
+int zbc_rank_widths(const zbc_mlp* model, const float* features, int ncols, const zbc_grid* g, int oversample,
+                    int32_t* widths_host, zbc_stream stream);
+
+/*
  * zbc_matvec -- Y = Z X (Algorithm 1, Sec. III.B).  With ACA storage (Z = U V^H) the library
  * first forms X' = V^H X (r_c x p) and runs Algorithm 1 on U (Sec. III.B, last paragraph).
  *   X : device complex64, m x p, column-major, ldx >= m

@@ -251,3 +251,21 @@ def cn01(shape, seed: int, dtype=np.complex128) -> np.ndarray:
 def gaussian_sketch(rows: int, cols: int, seed: int) -> np.ndarray:
     """Complex Gaussian test matrix for randomized range finding (column-major, complex128)."""
     return cn01((rows, cols), seed)
+
+
+def mode_sketches(grid: Grid, width: int, seed: int, dtype=np.complex64):
+    """The three test matrices Omega_g (N_g x width) for a grid, N_1 = n2 n3, N_2 = n1 n3,
+    N_3 = n1 n2 (rounded to dtype: both the GPU and the oracle use these exact values)."""
+    n1, n2, n3 = grid.shape
+    return [gaussian_sketch(r, width, seed + i).astype(dtype) for i, r in enumerate((n2 * n3, n1 * n3, n1 * n2))]
+
+
+LENGTH_SCALE = 0.1  # metres, scale of the position features
+
+
+def rank_features(grid: Grid, segs: Segments) -> np.ndarray:
+    """Per-segment geometry features (m x 7, float32): centre / 0.1 m, unit tangent, distance
+    to the voxel box / 0.1 m."""
+    d = bbox_distance(grid, segs.centre)
+    f = np.concatenate([segs.centre / LENGTH_SCALE, segs.tangent, (d / LENGTH_SCALE)[:, None]], axis=1)
+    return f.astype(np.float32)

@@ -85,6 +85,17 @@ def lib():
             "zbc_tc_selftest": ([vp, vp, vp, i32, i32, i32], i32),
             "aca_compress": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, i32, dbl, i32, i32, dbl,
                               C.POINTER(vp), C.POINTER(zbc_aca_stats), vp, vp], i32),
+            "tucker_compress_randomized": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, vp, vp, vp, vp, i32,
+                                            C.POINTER(vp), C.POINTER(zbc_compress_stats), vp], i32),
+            "zbc_mlp_num_params": ([], i32),
+            "zbc_mlp_create": ([vp, i32, C.POINTER(vp)], i32),
+            "zbc_mlp_free": ([vp], i32),
+            "zbc_mlp_get_params": ([vp, vp, vp], i32),
+            "zbc_mlp_forward": ([vp, vp, i32, vp, vp], i32),
+            "zbc_mlp_backward": ([vp, vp, vp, i32, vp, vp, vp], i32),
+            "zbc_mlp_adam_step": ([vp, vp, C.c_float, vp], i32),
+            "zbc_mlp_train": ([vp, vp, vp, i32, i32, C.c_float, vp, vp], i32),
+            "zbc_rank_widths": ([vp, vp, i32, C.POINTER(zbc_grid), i32, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -299,6 +310,77 @@ def aca_compress(grid, dsegs: DeviceSegments, freq_hz: float, tol: float, max_ra
     _check(lib().aca_compress(C.byref(g), C.byref(s), freq_hz, q, tol, max_rank, mode, tucker_tol, C.byref(h),
                               C.byref(st), piv.ctypes.data_as(C.c_void_p), _stream(stream)))
     return Handle(h), st, piv[:2 * st.rank].reshape(-1, 2)
+
+
+def tucker_compress_randomized(cols, grid, tol: float, widths: np.ndarray, sketches, lmax: int, q=3,
+                               append_to: Handle | None = None, stream=None):
+    """widths: int32[3*ncols*q]; sketches: three complex64 CUDA tensors holding Omega_g
+    column-major (shape (lmax, N_g)).  Returns (Handle, stats)."""
+    import torch
+    g = grid_struct(grid)
+    dt = C128 if cols.dtype == torch.complex128 else C64
+    wdt = np.ascontiguousarray(widths, dtype=np.int32)
+    h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
+    st = zbc_compress_stats()
+    _check(lib().tucker_compress_randomized(_ptr(cols), _ld(cols), cols.shape[0], C.byref(g), q, dt, tol,
+                                            wdt.ctypes.data_as(C.c_void_p), _ptr(sketches[0]), _ptr(sketches[1]),
+                                            _ptr(sketches[2]), lmax, C.byref(h), C.byref(st), _stream(stream)))
+    return (append_to if append_to is not None else Handle(h)), st
+
+
+class Mlp:
+    """Owns a zbc_mlp* (rank predictor)."""
+
+    def __init__(self, params: np.ndarray):
+        n = int(lib().zbc_mlp_num_params())
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == n, (p.size, n)
+        self.ptr = C.c_void_p()
+        _check(lib().zbc_mlp_create(p.ctypes.data_as(C.c_void_p), n, C.byref(self.ptr)))
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().zbc_mlp_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+    def params(self):
+        a = np.zeros(self.n, dtype=np.float32)
+        b = np.zeros(self.n, dtype=np.float32)
+        _check(lib().zbc_mlp_get_params(self.ptr, a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p)))
+        return a, b
+
+    def forward(self, X, stream=None):
+        import torch
+        out = torch.empty((X.shape[0], 9), dtype=torch.float32, device=X.device)
+        _check(lib().zbc_mlp_forward(self.ptr, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def backward(self, X, T, stream=None):
+        import torch
+        g = torch.empty(self.n, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().zbc_mlp_backward(self.ptr, _ptr(X), _ptr(T), X.shape[0], _ptr(g), _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def adam_step(self, grads, lr, stream=None):
+        _check(lib().zbc_mlp_adam_step(self.ptr, _ptr(grads), lr, _stream(stream)))
+
+    def train(self, X, T, steps, lr, stream=None):
+        import torch
+        hist = torch.empty(steps, dtype=torch.float32, device=X.device)
+        _check(lib().zbc_mlp_train(self.ptr, _ptr(X), _ptr(T), X.shape[0], steps, lr, _ptr(hist), _stream(stream)))
+        return hist
+
+    def widths(self, features, grid, oversample=4, stream=None):
+        g = grid_struct(grid)
+        w = np.zeros(9 * features.shape[0], dtype=np.int32)
+        _check(lib().zbc_rank_widths(self.ptr, _ptr(features), features.shape[0], C.byref(g), oversample,
+                                     w.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return w
 
 
 def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):

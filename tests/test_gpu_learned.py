@@ -1,0 +1,145 @@
+"""Learned part on the GPU: MLP forward/backward/Adam against the FP64 oracle (same bf16-rounded
+weights), randomized Tucker against the oracle's randomized Tucker (same widths and sketches),
+the HOSVD fallback, and the learned-width pipeline end to end."""
+import numpy as np
+import pytest
+
+from oracle import greens, mlp, randomized, tucker
+from paper_2103_06393_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import __graft_entry__  # noqa: E402
+
+__graft_entry__.build()
+from paper_2103_06393_gb300 import zbc  # noqa: E402
+
+
+def pack(params):
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in params]).astype(np.float32)
+
+
+def unpack(vec):
+    out, o = [], 0
+    for i in range(4):
+        fi, fo = mlp.SIZES[i], mlp.SIZES[i + 1]
+        W = vec[o:o + fi * fo].reshape(fo, fi).astype(np.float64)
+        o += fi * fo
+        b = vec[o:o + fo].astype(np.float64)
+        o += fo
+        out.append((W, b))
+    return out
+
+
+def test_mlp_forward_backward_against_oracle():
+    params = mlp.init_params(0)
+    M = zbc.Mlp(pack(params))
+    master, wbf = M.params()
+    pbf = unpack(wbf)                       # the bf16-rounded weights the GPU computes with
+    assert np.max(np.abs(wbf - pack(params))) <= 2 ** -8 * np.max(np.abs(pack(params)))
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(77, 7)).astype(np.float32)   # ragged: 77 = 2*32 + 13
+    T = rng.normal(size=(77, 9)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    out = M.forward(Xd).cpu().numpy()
+    ref, cache = mlp.forward(pbf, X.astype(np.float64))
+    assert np.max(np.abs(out - ref)) <= 1e-5 * np.max(np.abs(ref))
+    g, loss = M.backward(Xd, Td)
+    grads = mlp.backward(pbf, cache, ref, T.astype(np.float64))
+    gref = np.concatenate([np.concatenate([gw.reshape(-1), gb]) for gw, gb in grads])
+    gg = g.cpu().numpy()
+    assert np.max(np.abs(gg - gref)) <= 1e-4 * np.max(np.abs(gref))
+    assert abs(float(loss.item()) - mlp.loss(ref, T)) <= 1e-5 * mlp.loss(ref, T)
+    # deterministic reduction: a second backward gives identical bits
+    g2, _ = M.backward(Xd, Td)
+    assert torch.equal(g, g2)
+    # one Adam step on the master weights
+    M.adam_step(g, 1e-3)
+    new_master, _ = M.params()
+    state = {}
+    upd = mlp.adam_step(unpack(master), _split(gg), state, lr=1e-3)
+    assert np.max(np.abs(new_master - pack(upd))) <= 1e-6
+
+
+def _split(vec):
+    out, o = [], 0
+    for i in range(4):
+        fi, fo = mlp.SIZES[i], mlp.SIZES[i + 1]
+        out.append((vec[o:o + fi * fo].reshape(fo, fi).astype(np.float64), vec[o + fi * fo:o + fi * fo + fo].astype(np.float64)))
+        o += fi * fo + fo
+    return out
+
+
+def test_mlp_training_reduces_loss():
+    params = mlp.init_params(3)
+    M = zbc.Mlp(pack(params))
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(256, 7)).astype(np.float32)
+    T = np.tanh(X @ rng.normal(size=(7, 9))).astype(np.float32)
+    hist = M.train(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), 300, 3e-3).cpu().numpy()
+    assert hist[-1] < 0.2 * hist[0]
+
+
+def _columns(name, n, m, dtype=torch.complex128):
+    w = inputs.scaled_workload(name, n, m=m)
+    g, s = w.grid, w.segments
+    ds = zbc.DeviceSegments(s)
+    cols = torch.arange(s.m, dtype=torch.int32, device="cuda")
+    Z = zbc.colmajor(3 * g.nv, s.m, dtype)
+    zbc.vsie_assemble_columns(g, ds, w.freq_hz, cols, Z)
+    torch.cuda.synchronize()
+    return w, g, s, Z
+
+
+def test_randomized_against_oracle_and_fallback():
+    w, g, s, Zd = _columns("precision", (24, 22, 20), 6)
+    Z = zbc.from_colmajor(Zd)
+    tol = 1e-6
+    lmax = 32
+    sk = inputs.mode_sketches(g, lmax, seed=11)
+    skd = [zbc.to_colmajor(o) for o in sk]
+    # widths from the oracle's HOSVD ranks + 4, except two tensors starved on purpose
+    widths = np.zeros(3 * 3 * s.m, dtype=np.int32)
+    hos = []
+    for j in range(s.m):
+        for k in range(3):
+            A = tucker.fold(Z[k * g.nv:(k + 1) * g.nv, j], g.shape)
+            _, _, info = tucker.hosvd(A, tol)
+            hos.append(info)
+            t = 3 * j + k
+            widths[3 * t:3 * t + 3] = [min(r + 4, n) // 2 * 2 for r, n in zip(info["ranks"], g.shape)]
+    widths[0:3] = 2
+    widths[3 * 7:3 * 7 + 3] = 2
+    h, st = zbc.tucker_compress_randomized(Zd, g, tol, widths, skd, lmax)
+    tens, _ = h.tensors()
+    assert st.n_fallback >= 2
+    for j in range(s.m):
+        for k in range(3):
+            t = 3 * j + k
+            A = tucker.fold(Z[k * g.nv:(k + 1) * g.nv, j], g.shape)
+            Go, Uo, info = randomized.randomized_tucker(A, widths[3 * t:3 * t + 3],
+                                                         [o.astype(np.complex128) for o in sk], tol)
+            gr = tuple(U.shape[1] for U in tens[j][k][1])
+            if info["fallback"]:
+                assert gr == hos[t]["ranks"] or min(hos[t]["margin"]) < 1e-5
+            elif min(info["margin"]) > 1e-3:
+                assert gr == info["ranks"], (t, gr, info["ranks"])
+            err = np.linalg.norm(tucker.reconstruct(tens[j][k][0], tens[j][k][1]) - A) / np.linalg.norm(A)
+            assert err <= tol * (1 + 1e-6) + 3e-7, (t, err)
+    assert st.max_rel_err <= tol * (1 + 1e-9)
+
+
+def test_learned_pipeline_end_to_end():
+    w, g, s, Zd = _columns("precision", (24, 22, 20), 8)
+    M = zbc.Mlp(pack(mlp.init_params(5)))
+    feats = torch.from_numpy(inputs.rank_features(g, s)).cuda()
+    widths = M.widths(feats, g, oversample=4)
+    assert widths.shape == (9 * s.m,) and widths.min() >= 2
+    lmax = 64
+    skd = [zbc.to_colmajor(o) for o in inputs.mode_sketches(g, lmax, seed=3)]
+    h, st = zbc.tucker_compress_randomized(Zd, g, 1e-6, widths, skd, lmax)
+    assert st.n_tensors == 3 * s.m and st.max_rel_err <= 1e-6 * (1 + 1e-9)
