@@ -172,7 +172,7 @@ int aca_compress(const zbc_grid* g, const zbc_segments* s, double freq_hz, int q
  * tucker_compress_randomized -- column-wise Tucker compression by a fixed-width randomized range
  * finder with an HOSVD fallback (no counterpart in the paper; Halko-Martinsson-Tropp range finder
  * per mode, as in the randomized HOSVD of Minster-Saibaba-Kilmer).  Per tensor t = j*q + k and
- * mode g: Y = A_(g) Omega_g[:, :w] (FP32 sketch), Q = orth(Y) (FP64 Householder),
+ * mode g: Y = A_(g) Omega_g[:, :w] (FP64 sketch), Q = orth(Y) (FP64 Householder),
  * C = A x1 Q1^H x2 Q2^H x3 Q3^H, e^2 = ||A||^2 - ||C||^2 (FP64).  If e^2 > tol^2 ||A||^2 the
  * tensor is recompressed by truncated HOSVD (counted in stats n_fallback); otherwise C is
  * truncated by HOSVD with the remaining budget (tol^2||A||^2 - e^2)/3 per mode and U_g = Q_g W_g,

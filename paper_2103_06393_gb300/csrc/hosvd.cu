@@ -610,7 +610,7 @@ int hosvd_compress(const void* cols, int64_t ld, int ncols, int n1, int n2, int 
 // ---------------------------------------------------------------------------------------------
 // Randomized range-finder Tucker with fixed widths and an HOSVD fallback (not in the paper;
 // Halko-Martinsson-Tropp range finder per mode as in the randomized HOSVD of Minster, Saibaba
-// and Kilmer):  Y_g = A_(g) Omega_g[:, :w_g] (FP32 sketch),  Q_g = orth(Y_g) (FP64 Householder),
+// and Kilmer):  Y_g = A_(g) Omega_g[:, :w_g] (FP64 sketch),  Q_g = orth(Y_g) (FP64 Householder),
 // C = A x1 Q1^H x2 Q2^H x3 Q3^H, e^2 = ||A||^2 - ||C||^2 (FP64).  If e^2 > tol^2 ||A||^2 the
 // widths failed and the tensor is redone by HOSVD; otherwise C is truncated by HOSVD with the
 // remaining budget (tol^2 ||A||^2 - e^2)/3 per mode, U_g = Q_g W_g.  Error <= tol ||A||_F.
@@ -627,47 +627,51 @@ struct SketchJob {
   double2* Y;        // n x w, ld n
 };
 
-// Y(x, l) = sum_c A(x, c) Omega(c, l)   (FP32 arithmetic, FP64 output)
+// Y(x, l) = sum_c A(x, c) Omega(c, l) in FP64.  (An FP32 sketch measured e^2 ~ 1e-13 ||A||^2 of
+// rounding noise on the 2 mm workloads, a sixth of the tol^2 = 1e-12 budget at tol 1e-6, which
+// inflated ranks; in FP64 the noise floor is far below the budget.)
 template <typename T>
 __global__ void __launch_bounds__(256) sketch_kernel(const SketchJob* jobs) {
   const SketchJob jb = jobs[blockIdx.y];
   const int x0 = blockIdx.x * 32;
   if (x0 >= jb.n) return;
-  __shared__ float2 sa[32][33];
-  __shared__ float2 so[32][kWmax + 1];
+  __shared__ double2 sa[16][33];
+  __shared__ double2 so[16][kWmax + 1];
   const int lx = threadIdx.x % 32, lg = threadIdx.x / 32;
-  float2 acc[kWmax / 8];
+  double2 acc[kWmax / 8];
 #pragma unroll
-  for (int i = 0; i < kWmax / 8; ++i) acc[i] = make_float2(0.f, 0.f);
-  for (int64_t c0 = 0; c0 < jb.C; c0 += 32) {
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+  for (int i = 0; i < kWmax / 8; ++i) acc[i] = make_double2(0.0, 0.0);
+  for (int64_t c0 = 0; c0 < jb.C; c0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
       const int cc = e / 32, xx = e % 32;
       const int64_t c = c0 + cc;
-      float2 v = make_float2(0.f, 0.f);
-      if (c < jb.C && x0 + xx < jb.n) {
-        const double2 d = ld_z<T>(jb.A, jb.u.at(x0 + xx, c));
-        v = make_float2((float)d.x, (float)d.y);
-      }
+      double2 v = make_double2(0.0, 0.0);
+      if (c < jb.C && x0 + xx < jb.n) v = ld_z<T>(jb.A, jb.u.at(x0 + xx, c));
       sa[cc][xx] = v;
     }
-    for (int e = threadIdx.x; e < 32 * kWmax; e += 256) {
+    for (int e = threadIdx.x; e < 16 * kWmax; e += 256) {
       const int cc = e / kWmax, l = e % kWmax;
       const int64_t c = c0 + cc;
-      so[cc][l] = (c < jb.C && l < jb.w) ? jb.Om[c + jb.ldo * l] : make_float2(0.f, 0.f);
+      double2 v = make_double2(0.0, 0.0);
+      if (c < jb.C && l < jb.w) {
+        const float2 o = jb.Om[c + jb.ldo * l];
+        v = make_double2(o.x, o.y);
+      }
+      so[cc][l] = v;
     }
     __syncthreads();
 #pragma unroll 4
-    for (int cc = 0; cc < 32; ++cc) {
-      const float2 a = sa[cc][lx];
+    for (int cc = 0; cc < 16; ++cc) {
+      const double2 a = sa[cc][lx];
 #pragma unroll
-      for (int i = 0; i < kWmax / 8; ++i) acc[i] = cfma(a, so[cc][lg + 8 * i], acc[i]);
+      for (int i = 0; i < kWmax / 8; ++i) acc[i] = zfma(a, so[cc][lg + 8 * i], acc[i]);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < kWmax / 8; ++i) {
     const int l = lg + 8 * i;
-    if (x0 + lx < jb.n && l < jb.w) jb.Y[(x0 + lx) + (int64_t)jb.n * l] = make_double2(acc[i].x, acc[i].y);
+    if (x0 + lx < jb.n && l < jb.w) jb.Y[(x0 + lx) + (int64_t)jb.n * l] = acc[i];
   }
 }
 
