@@ -245,6 +245,26 @@ int zbc_matvec(const zbc_handle* h, const void* X, int64_t ldx, int p, void* Y, 
 int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi,
                 int64_t ldpsi, zbc_precision prec, zbc_stream stream);
 
+/*
+ * zbc_rmatvec_noalloc -- Psi = Z^H Phi in FP32 on CUDA cores, like zbc_rmatvec with
+ * ZBC_FP32_SIMT, but without allocating any memory.  The paper has no counterpart: this exists
+ * for callers that cannot allocate device memory at the moment they need the product (inside a
+ * CUDA graph capture, where cudaMalloc is not allowed; real-time or embedded loops whose memory
+ * is fixed up front; allocator callbacks that must not re-enter the allocator).
+ *   - Partial sums live in one scratch array compiled into the library: 16 MiB of device memory
+ *     on every GPU that loads the library, held until the process exits.  Calls whose q*M*p
+ *     (+ M*p for ACA storage) complex64 values exceed it are rejected with ZBC_EINVAL.
+ *   - The handle's decompression cache must already exist: call zbc_matvec or zbc_rmatvec on the
+ *     handle once first (that call allocates); otherwise ZBC_EINVAL.
+ *   - The scratch array's device address is looked up on the first call made on each device
+ *     (with that device current); make that first call before any stream capture begins.
+ *   - All calls share the array and it keeps the last call's contents; each call overwrites all
+ *     it reads, so it needs no clearing, but calls that overlap on the GPU race on it.
+ * Arguments are those of zbc_rmatvec.
+ */
+int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi, int64_t ldpsi,
+                        zbc_stream stream);
+
 /* Release a handle and its device memory (NULL is accepted). */
 int zbc_free(zbc_handle* h);
 

@@ -298,6 +298,50 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   return reduce_partials(partial, G * h.q, h.M, p, out, ldo, st);
 }
 
+// The same adjoint with caller-provided scratch for the partial sums and no allocation at all:
+// the decompression cache must already exist, and the number of partial-sum groups is capped
+// so that they fit scratch_bytes.
+template <int PS>
+static int launch_rmatvec_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
+                                  float2* scratch, size_t scratch_bytes, cudaStream_t st) {
+  const int R = h.cache_r;
+  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
+  const int NV = 2 * PS;
+  const size_t base = ChunkSmem::bytes(R, g.NUp) + sizeof(float) * kChunk * 8 * NV;
+  const size_t budget = 220 * 1024 - base;
+  const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
+  const int jblocks = ceil_div(h.M, MJ);
+  const int schunks = ceil_div(p, PS);
+  const size_t per_group = sizeof(float2) * (size_t)h.q * h.M * p;
+  const int gmax = (int)std::min<size_t>(scratch_bytes / per_group, 1 << 20);
+  ZBC_CHECK_ARG(gmax >= 1, "scratch of %zu bytes cannot hold one partial-sum group (%zu bytes)", scratch_bytes,
+                per_group);
+  int G = std::max(1, 2 * sm_count() / std::max(1, h.q * jblocks * schunks));
+  G = std::min(std::min(G, g.ntiles()), gmax);
+  const size_t sm = base + sizeof(float) * (size_t)MJ * NV;
+  ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT adjoint", R);
+  ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  dim3 grid(G, h.q * jblocks, schunks);
+  rmatvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
+                                                      p, scratch);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);
+}
+
+int rmatvec_simt_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
+                         float2* scratch, size_t scratch_bytes, cudaStream_t st) {
+  if (!h.cache) {
+    set_error("the handle's decompression cache is not built: call zbc_matvec or zbc_rmatvec on it once first");
+    return ZBC_EINVAL;
+  }
+  if (p == 1) return launch_rmatvec_scratch<1>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p == 2) return launch_rmatvec_scratch<2>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 4) return launch_rmatvec_scratch<4>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 8) return launch_rmatvec_scratch<8>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  return launch_rmatvec_scratch<16>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+}
+
 int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
   if (p == 1) return launch_matvec<1>(h, X, ldx, p, Y, ldy, st);
   if (p == 2) return launch_matvec<2>(h, X, ldx, p, Y, ldy, st);

@@ -96,6 +96,7 @@ def lib():
             "zbc_mlp_adam_step": ([vp, vp, C.c_float, vp], i32),
             "zbc_mlp_train": ([vp, vp, vp, i32, i32, C.c_float, vp, vp], i32),
             "zbc_rank_widths": ([vp, vp, i32, C.POINTER(zbc_grid), i32, vp, vp], i32),
+            "zbc_rmatvec_noalloc": ([vp, vp, i64, i32, vp, i64, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -388,6 +389,15 @@ def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):
     p = X.shape[0]
     _check(lib().zbc_matvec(h.ptr, _ptr(X), _ld(X), p, _ptr(Y), _ld(Y), prec, _stream(stream)))
     return Y
+
+
+def zbc_rmatvec_noalloc(h: Handle, Phi, Psi, stream=None):
+    """Psi = Z^H Phi (FP32) using the library's fixed scratch array instead of allocating: for
+    callers that cannot allocate at call time (e.g. during CUDA graph capture).  The handle
+    needs one earlier zbc_matvec / zbc_rmatvec call."""
+    p = Phi.shape[0]
+    _check(lib().zbc_rmatvec_noalloc(h.ptr, _ptr(Phi), _ld(Phi), p, _ptr(Psi), _ld(Psi), _stream(stream)))
+    return Psi
 
 
 def zbc_rmatvec(h: Handle, Phi, Psi, prec=FP32_SIMT, stream=None):
