@@ -11,6 +11,8 @@
 // U1 row a thread loads serves kUQ voxels.
 #pragma once
 
+#include <algorithm>
+
 #include "zbc_internal.cuh"
 
 namespace zbc {
@@ -19,7 +21,7 @@ constexpr int kChunk = 8;      // columns per chunk
 constexpr int kThreads = 256;  // threads per CTA
 constexpr int kUQ = 4;         // u values per task
 constexpr int kRmax = 32;      // largest rank r1 the product kernels accept
-constexpr int kWPre = 8;       // W values each thread prefetches per chunk (kChunk*kRmax*NUp/kThreads max)
+constexpr int kWPre = 8;       // W values each front-end thread prefetches per chunk
 
 // per-tensor view of the decompression cache
 struct CacheDesc {
@@ -61,8 +63,9 @@ inline Geo make_geo(int n1, int n2, int n3, int R, int max_tasks, int max_rows =
   if (tasks * kUQ * 32 > max_rows) tasks = max_rows / (kUQ * 32);
   int nq = tasks / g.nb32;
   if (nq < 1) nq = 1;
-  const int nq_pre = (kWPre * kThreads) / (kChunk * R * kUQ);
-  if (nq > nq_pre) nq = nq_pre < 1 ? 1 : nq_pre;
+  // the chunk's W blocks (kChunk x R x 4nq) must fit the register prefetch of the CTA's
+  // 32 * max(4, ntask) front-end threads
+  while (nq > 1 && kChunk * R * kUQ * nq > kWPre * 32 * std::max(4, g.nb32 * nq)) --nq;
   int nu = nq * kUQ;
   const int n2r = (n2 + kUQ - 1) / kUQ * kUQ;
   if (nu > n2r) nu = n2r;
@@ -79,7 +82,7 @@ inline Geo make_geo(int n1, int n2, int n3, int R, int max_tasks, int max_rows =
 struct ChunkSmem {
   float2* W;
   CacheDesc* cd;
-  static size_t bytes(int R, int NUp) {
+  __host__ __device__ static size_t bytes(int R, int NUp) {
     return sizeof(float2) * (size_t)kChunk * R * NUp + sizeof(CacheDesc) * kChunk;
   }
   __device__ __forceinline__ unsigned char* carve(unsigned char* base, int R, int NUp) {
@@ -89,18 +92,42 @@ struct ChunkSmem {
   }
 };
 
+// Two front-end buffers (chunk c uses buffer c & 1) with a per-chunk staging area of xn complex
+// values after each, addressed arithmetically (no local-memory arrays of pointers).
+struct FrontEnd2 {
+  unsigned char* base;
+  size_t stride;
+  int R, NUp;
+  __host__ __device__ static size_t buf_bytes(int R, int NUp, int xn) {
+    return (ChunkSmem::bytes(R, NUp) + sizeof(float2) * (size_t)xn + 15) / 16 * 16;
+  }
+  __device__ __forceinline__ FrontEnd2(unsigned char* b, int R_, int NUp_, int xn)
+      : base(b), stride(buf_bytes(R_, NUp_, xn)), R(R_), NUp(NUp_) {}
+  __device__ __forceinline__ ChunkSmem cs(int b) const {
+    ChunkSmem s;
+    s.carve(base + b * stride, R, NUp);
+    return s;
+  }
+  __device__ __forceinline__ float2* xs(int b) const {
+    return (float2*)(base + b * stride + ChunkSmem::bytes(R, NUp));
+  }
+  __device__ __forceinline__ unsigned char* end() const { return base + 2 * stride; }
+};
+
 // Register prefetch of one chunk's W blocks: element e = (jj, a, u) of W[jj][a][NUp].
 // Loaded one chunk ahead so the global-memory latency overlaps the current chunk's work.
+// tid / nthr: this thread's index among the nthr threads that share the prefetch.
 struct WPrefetch {
   float2 v[kWPre];
-  CacheDesc cd;  // cache entry of column jj = threadIdx.x (threads < kChunk)
+  CacheDesc cd;  // cache entry of column jj = tid (threads tid < kChunk)
   __device__ __forceinline__ void load(const float2* __restrict__ wc, const CacheDesc* __restrict__ cdesc,
-                                       const Geo& g, int R, int q, int k, int j0, int jc, int i2_0, int i3) {
-    if (threadIdx.x < jc) cd = cdesc[(int64_t)(j0 + threadIdx.x) * q + k];
+                                       const Geo& g, int R, int q, int k, int j0, int jc, int i2_0, int i3, int tid,
+                                       int nthr) {
+    if (tid < jc) cd = cdesc[(int64_t)(j0 + tid) * q + k];
     const int per = R * g.NUp;
 #pragma unroll
     for (int i = 0; i < kWPre; ++i) {
-      const int e = threadIdx.x + i * kThreads;
+      const int e = tid + i * nthr;
       float2 x = make_float2(0.f, 0.f);
       if (e < kChunk * per) {
         const int jj = e / per, rem = e % per;
@@ -113,14 +140,14 @@ struct WPrefetch {
       v[i] = x;
     }
   }
-  __device__ __forceinline__ void store(const ChunkSmem& s, const Geo& g, int R, int jc) const {
+  __device__ __forceinline__ void store(const ChunkSmem& s, const Geo& g, int R, int jc, int tid, int nthr) const {
     const int per = R * g.NUp;
 #pragma unroll
     for (int i = 0; i < kWPre; ++i) {
-      const int e = threadIdx.x + i * kThreads;
+      const int e = tid + i * nthr;
       if (e < kChunk * per) s.W[e] = v[i];
     }
-    if (threadIdx.x < jc) s.cd[threadIdx.x] = cd;
+    if (tid < jc) s.cd[tid] = cd;
   }
 };
 

@@ -20,11 +20,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                        int R, const float2* __restrict__ X, int64_t ldx, int p, float2* __restrict__ Y,
                        int64_t ldy) {
   extern __shared__ __align__(16) unsigned char smem[];
-  ChunkSmem cs;
-  float2* xs = (float2*)cs.carve(smem, R, g.NUp);  // [kChunk][PS]
+  // two front-end buffers (chunk c uses buffer c & 1), so one barrier per chunk suffices
+  const FrontEnd2 fe(smem, R, g.NUp, kChunk * PS);
   const int k = blockIdx.y;
   const int s0 = blockIdx.z * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   int i1_0, i2_0, i3;
   g.tile(blockIdx.x, i1_0, i2_0, i3);
   const bool active = warp < g.ntask;
@@ -37,16 +38,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int i = 0; i < PS; ++i) acc[l][i] = make_float2(0.f, 0.f);
   WPrefetch pf;
-  pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3);
-  for (int j0 = 0; j0 < M; j0 += kChunk) {
+  pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3, tid, nthr);
+  for (int j0 = 0, c = 0; j0 < M; j0 += kChunk, ++c) {
     const int jc = min(kChunk, M - j0);
-    for (int e = threadIdx.x; e < jc * PS; e += blockDim.x) {
+    const int b = c & 1;
+    const ChunkSmem cs = fe.cs(b);
+    float2* xs = fe.xs(b);
+    for (int e = tid; e < jc * PS; e += nthr) {
       const int jj = e / PS, i = e % PS;
       xs[e] = (s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
     }
-    pf.store(cs, g, R, jc);
+    pf.store(cs, g, R, jc, tid, nthr);
     __syncthreads();
-    if (j0 + kChunk < M) pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3);
+    if (j0 + kChunk < M)
+      pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3, tid, nthr);
     if (active) {
       for (int jj = 0; jj < jc; ++jj) {
         const CacheDesc d = cs.cd[jj];
@@ -60,7 +65,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    __syncthreads();
   }
   if (!active || !ok) return;
   const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
@@ -118,17 +122,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int NV = 2 * PS;
   constexpr int SH = 5 - Log2<NV>::v;
   extern __shared__ __align__(16) unsigned char smem[];
-  ChunkSmem cs;
-  float* red = (float*)cs.carve(smem, R, g.NUp);  // [kChunk][8][NV]
-  float* pacc = red + kChunk * 8 * NV;              // [MJ][NV]
+  const int nw = blockDim.x >> 5;
+  const FrontEnd2 fe(smem, R, g.NUp, 0);   // chunk c uses buffer c & 1
+  float* red = (float*)fe.end();            // [kChunk][nw][NV]
+  float* pacc = red + kChunk * nw * NV;     // [MJ][NV]
   const int k = blockIdx.y % q;
   const int jb0 = (blockIdx.y / q) * MJ;
   const int jb1 = min(M, jb0 + MJ);
   const int s0 = blockIdx.z * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
   const bool active = warp < g.ntask;
   for (int e = threadIdx.x; e < (jb1 - jb0) * NV; e += blockDim.x) pacc[e] = 0.f;
+  int c = 0;
   for (int t = blockIdx.x; t < g.ntiles(); t += gridDim.x) {
     int i1_0, i2_0, i3;
     g.tile(t, i1_0, i2_0, i3);
@@ -146,12 +153,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         ph[l][i] = (okl && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
     }
     WPrefetch pf;
-    pf.load(cache, cdesc, g, R, q, k, jb0, min(kChunk, jb1 - jb0), i2_0, i3);
-    for (int j0 = jb0; j0 < jb1; j0 += kChunk) {
+    pf.load(cache, cdesc, g, R, q, k, jb0, min(kChunk, jb1 - jb0), i2_0, i3, tid, nthr);
+    for (int j0 = jb0; j0 < jb1; j0 += kChunk, ++c) {
       const int jc = min(kChunk, jb1 - j0);
-      pf.store(cs, g, R, jc);
+      const ChunkSmem cs = fe.cs(c & 1);
+      pf.store(cs, g, R, jc, tid, nthr);
       __syncthreads();
-      if (j0 + kChunk < jb1) pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, jb1 - j0 - kChunk), i2_0, i3);
+      if (j0 + kChunk < jb1)
+        pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, jb1 - j0 - kChunk), i2_0, i3, tid, nthr);
       for (int jj = 0; jj < jc; ++jj) {
         const CacheDesc d = cs.cd[jj];
         float2 z[kUQ];
@@ -170,19 +179,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           vals[2 * i + 1] = im;
         }
         const float r = warp_reduce_scatter<NV>(vals, lane);
-        if ((lane & ((1 << SH) - 1)) == 0) red[(jj * 8 + warp) * NV + (lane >> SH)] = r;
+        if ((lane & ((1 << SH) - 1)) == 0) red[(jj * nw + warp) * NV + (lane >> SH)] = r;
       }
       __syncthreads();
       for (int e = threadIdx.x; e < jc * NV; e += blockDim.x) {
         const int jj = e / NV, i = e % NV;
         float tsum = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) tsum += red[(jj * 8 + w) * NV + i];
+        for (int w = 0; w < nw; ++w) tsum += red[(jj * nw + w) * NV + i];
         pacc[(j0 + jj - jb0) * NV + i] += tsum;
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
   float2* out = partial + (int64_t)(blockIdx.x * q + k) * M * p;
   for (int e = threadIdx.x; e < (jb1 - jb0) * PS; e += blockDim.x) {
     const int jl = e % (jb1 - jb0), i = e / (jb1 - jb0);
@@ -250,7 +258,8 @@ static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2*
   ZBC_TRY(build_decomp_cache(h, st));
   const int R = h.cache_r;
   Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
-  const size_t sm = ChunkSmem::bytes(R, g.NUp) + sizeof(float2) * kChunk * PS;
+  const int nthr = 32 * std::max(4, g.ntask);
+  const size_t sm = 2 * FrontEnd2::buf_bytes(R, g.NUp, kChunk * PS);
   static bool attr_set = false;
   if (!attr_set) {
     ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
@@ -258,7 +267,7 @@ static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2*
   }
   ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT path", R);
   dim3 grid(g.ntiles(), h.q, ceil_div(p, PS));
-  matvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, X, ldx, p, Y,
+  matvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, X, ldx, p, Y,
                                                      ldy);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
@@ -272,7 +281,8 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   const int R = h.cache_r;
   Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
   const int NV = 2 * PS;
-  const size_t base = ChunkSmem::bytes(R, g.NUp) + sizeof(float) * kChunk * 8 * NV;
+  const int nthr = 32 * std::max(4, g.ntask);
+  const size_t base = 2 * FrontEnd2::buf_bytes(R, g.NUp, 0) + sizeof(float) * kChunk * (nthr / 32) * NV;
   // j-block so that the per-CTA accumulator stays within the shared-memory budget
   const size_t budget = 220 * 1024 - base;
   const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
@@ -291,8 +301,8 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)G * h.q * h.M * p));
   float2* partial = (float2*)h.work_partial.ptr;
   dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
-                                                      p, partial);
+  rmatvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
+                                                  p, partial);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(partial, G * h.q, h.M, p, out, ldo, st);
@@ -307,7 +317,8 @@ static int launch_rmatvec_scratch(Handle& h, const float2* Phi, int64_t ldphi, i
   const int R = h.cache_r;
   Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
   const int NV = 2 * PS;
-  const size_t base = ChunkSmem::bytes(R, g.NUp) + sizeof(float) * kChunk * 8 * NV;
+  const int nthr = 32 * std::max(4, g.ntask);
+  const size_t base = 2 * FrontEnd2::buf_bytes(R, g.NUp, 0) + sizeof(float) * kChunk * (nthr / 32) * NV;
   const size_t budget = 220 * 1024 - base;
   const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
   const int jblocks = ceil_div(h.M, MJ);
@@ -322,8 +333,8 @@ static int launch_rmatvec_scratch(Handle& h, const float2* Phi, int64_t ldphi, i
   ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT adjoint", R);
   ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, kThreads, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
-                                                      p, scratch);
+  rmatvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
+                                                  p, scratch);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);
