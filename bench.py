@@ -64,10 +64,17 @@ def build_handle(w, zbc, torch, batch_cols=256):
 
 
 def algorithmic_flops(h, w, p):
-    from oracle import products  # only for the count formula's ranks bookkeeping
+    """Real flops of one product by the complexity count of Table III (complex MAC = 8 flops):
+    per stored tensor the mode products of the decompression (n1 r1 r2 r3 + n1 n2 r2 r3 +
+    n_v r3 complex MACs), plus the contraction with the p right-hand sides (q n_v M p MACs)."""
     ranks, _, _ = h.export()
     inf = h.info()
-    return products.flops(ranks.reshape(-1, 3), w.grid.shape, inf.q, inf.M, p)
+    n1, n2, n3 = w.grid.shape
+    nv = n1 * n2 * n3
+    r = np.asarray(ranks, dtype=np.float64).reshape(-1, 3)
+    r1, r2, r3 = r[:, 0], r[:, 1], r[:, 2]
+    dec = float((n1 * r1 * r2 * r3 + n1 * n2 * r2 * r3 + nv * r3).sum())
+    return 8.0 * dec + 8.0 * inf.q * nv * inf.M * p
 
 
 # ---------------------------------------------------------------------------------------------
@@ -189,6 +196,8 @@ def run_zbc(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = inputs.workload(WORKLOAD)
+    if args.columns:
+        w = inputs.scaled_workload(WORKLOAD, w.grid.shape, m=args.columns)
     g = w.grid
     p = w.p
     h, t_build = build_handle(w, zbc, torch)
@@ -336,7 +345,7 @@ def run_zbc(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
-        "config": {"workload": "precision: 96^3 voxels (2 mm), 8-loop coil, 1024 segments, 298.2 MHz, "
+        "config": {"workload": f"precision: 96^3 voxels (2 mm), 8-loop coil, {w.segments.m} segments, 298.2 MHz, "
                                "HOSVD tol 1e-6, complex64 Tucker storage, p=16",
                    "forward": fwd_head, "adjoint": adj_head, "M": inf.M, "max_rank": inf.max_rank, "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas x{ws}"},
@@ -409,6 +418,8 @@ def main():
     ap.add_argument("--impl", default="zbc", choices=["zbc", "reference"])
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--columns", type=int, default=0,
+                    help="keep only the first N segments (smaller case for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -265,6 +265,16 @@ int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void
 int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi, int64_t ldpsi,
                         zbc_stream stream);
 
+/*
+ * zbc_product_status -- device-side status of this handle's product kernels (zbc_matvec,
+ * zbc_rmatvec, zbc_rmatvec_noalloc).  The products run asynchronously on `stream`; a product
+ * kernel whose bounded wait (on its copy pipeline or on the tensor cores) gave up returns early
+ * with its output incomplete and records that in a flag of the handle.  This call synchronises
+ * `stream` and returns ZBC_ETIMEOUT if the flag is set (clearing it), else ZBC_OK.  The paper
+ * has no counterpart.
+ */
+int zbc_product_status(const zbc_handle* h, zbc_stream stream);
+
 /* Release a handle and its device memory (NULL is accepted). */
 int zbc_free(zbc_handle* h);
 

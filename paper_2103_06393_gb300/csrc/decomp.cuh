@@ -1,14 +1,19 @@
 // Decompression front end shared by the product kernels (Sec. III.B, Eq. Tucker).
 //
 // Z^{kj} = G x1 U1 x2 U2 x3 U3.  The partial product W_j = G_j x2 U2_j x3 U3_j (r1 x n2 x n3)
-// does not depend on the right-hand sides, so a handle keeps it (and a row-major copy of
-// U1_j) in a device cache built once, on the first product call (decomp_cache.cu).  A product
-// CTA then owns a voxel tile of B1 (i1) x NU (i2) voxels at one i3 and walks the stored
-// columns in chunks of kChunk: it stages the chunk's W blocks in shared memory (prefetched one
-// chunk ahead in registers) and forms the last mode product
+// does not depend on the right-hand sides, so a handle keeps it (and a copy of U1_j blocked by
+// i1 tiles) in a device cache built once, on the first product call (decomp_cache.cu).  A
+// product CTA then owns a voxel tile of B1 (i1) x NU (i2) voxels at one i3 and walks the stored
+// columns, forming the last mode product
 //   Z[i1, u, j] = sum_a U1_j[i1, a] W_j[a, i2_0 + u, i3]
 // on CUDA cores.  A task is 32 consecutive i1 (one per lane) times kUQ consecutive u, so each
 // U1 row a thread loads serves kUQ voxels.
+//
+// Cache layout per tensor (all offsets even, so every block starts on 16 bytes):
+//   W  : [i3][i2][a], a < r1p (r1 rounded up to 2, the pad entry zero)
+//   U1 : [t1][a][i1 - t1 B1], a < r1p, i1 row stride B1p (B1 rounded up to 2), zero padded
+// so the U1 block of an i1 tile and the W block of an (i2 range, i3) are each one contiguous
+// run that a single bulk copy moves to shared memory.
 #pragma once
 
 #include <algorithm>
@@ -25,10 +30,20 @@ constexpr int kWPre = 8;       // W values each front-end thread prefetches per 
 
 // per-tensor view of the decompression cache
 struct CacheDesc {
-  int64_t woff;   // W: [i3][i2][a] complex64, r1 per (i2, i3)
-  int64_t uoff;   // U1 row-major: [i1][a], row stride r1p (r1 rounded up to 2)
+  int64_t woff;   // W: [i3][i2][a] complex64, r1p per (i2, i3)
+  int64_t uoff;   // U1: [t1][a][i1 local], r1p rows of B1p per i1 tile
   int r1, r1p;
 };
+
+// i1 tile extent: at most 128 rows (the 32-lane groups of four warps), balanced over the tiles
+// so that the last tile is not mostly padding
+__host__ __device__ inline int tile_b1(int n1) {
+  const int nb1 = (n1 + 127) / 128;
+  const int per = (n1 + nb1 - 1) / nb1;
+  const int b1 = (per + 31) / 32 * 32;
+  return n1 < b1 ? n1 : b1;
+}
+__host__ __device__ inline int tile_b1p(int n1) { return (tile_b1(n1) + 1) / 2 * 2; }
 
 struct Geo {
   int n1, n2, n3;
@@ -57,15 +72,15 @@ inline Geo make_geo(int n1, int n2, int n3, int R, int max_tasks, int max_rows =
   g.n1 = n1;
   g.n2 = n2;
   g.n3 = n3;
-  g.B1 = n1 < 128 ? n1 : 128;
+  g.B1 = tile_b1(n1);
   g.nb32 = (g.B1 + 31) / 32;
   int tasks = max_tasks;
   if (tasks * kUQ * 32 > max_rows) tasks = max_rows / (kUQ * 32);
   int nq = tasks / g.nb32;
   if (nq < 1) nq = 1;
   // the chunk's W blocks (kChunk x R x 4nq) must fit the register prefetch of the CTA's
-  // 32 * max(4, ntask) front-end threads
-  while (nq > 1 && kChunk * R * kUQ * nq > kWPre * 32 * std::max(4, g.nb32 * nq)) --nq;
+  // 32 * max(4, ntask) front-end threads (R = 0: no register prefetch)
+  while (R > 0 && nq > 1 && kChunk * R * kUQ * nq > kWPre * 32 * std::max(4, g.nb32 * nq)) --nq;
   int nu = nq * kUQ;
   const int n2r = (n2 + kUQ - 1) / kUQ * kUQ;
   if (nu > n2r) nu = n2r;
@@ -134,7 +149,7 @@ struct WPrefetch {
         const int a = rem / g.NUp, u = rem % g.NUp;
         if (jj < jc && u < g.NU && i2_0 + u < g.n2) {
           const CacheDesc d = cdesc[(int64_t)(j0 + jj) * q + k];
-          if (a < d.r1) x = __ldg(wc + d.woff + ((int64_t)i3 * g.n2 + i2_0 + u) * d.r1 + a);
+          if (a < d.r1) x = __ldg(wc + d.woff + ((int64_t)i3 * g.n2 + i2_0 + u) * d.r1p + a);
         }
       }
       v[i] = x;
@@ -153,17 +168,17 @@ struct WPrefetch {
 
 // Last mode product of one column for kUQ voxels sharing i1:
 //   z[l] = sum_a U1_j[i1, a] W_j[a][u0 + l]
-// U1 row loaded as float4 pairs from the row-major cache (all loads issued before use).
-__device__ __forceinline__ void last_mode4(const float2* __restrict__ u1row, int r1, bool ok, const float2* Wj,
+// u1 points at (a = 0, this lane's i1) of the cached U1 tile block (row stride B1p); all loads
+// are issued before use.
+__device__ __forceinline__ void last_mode4(const float2* __restrict__ u1, int B1p, int r1, bool ok, const float2* Wj,
                                            int NUp, int u0, float2 (&z)[kUQ]) {
 #pragma unroll
   for (int l = 0; l < kUQ; ++l) z[l] = make_float2(0.f, 0.f);
   if (!ok) return;
-  float4 ur[kRmax / 2];
-  const float4* src = reinterpret_cast<const float4*>(u1row);
+  float2 ur[kRmax];
 #pragma unroll
-  for (int i = 0; i < kRmax / 2; ++i)
-    if (2 * i < r1) ur[i] = __ldg(src + i);
+  for (int a = 0; a < kRmax; ++a)
+    if (a < r1) ur[a] = __ldg(u1 + (int64_t)a * B1p);
   const float4* w4 = reinterpret_cast<const float4*>(Wj + u0);
   const int stride4 = NUp / 2;
 #pragma unroll
@@ -173,7 +188,7 @@ __device__ __forceinline__ void last_mode4(const float2* __restrict__ u1row, int
     for (int h = 0; h < 2; ++h) {
       const int a = 2 * i + h;
       if (a >= r1) break;
-      const float2 x = h == 0 ? make_float2(ur[i].x, ur[i].y) : make_float2(ur[i].z, ur[i].w);
+      const float2 x = ur[a];
       const float4 wa = w4[a * stride4], wb = w4[a * stride4 + 1];
       z[0] = cfma(x, make_float2(wa.x, wa.y), z[0]);
       z[1] = cfma(x, make_float2(wa.z, wa.w), z[1]);

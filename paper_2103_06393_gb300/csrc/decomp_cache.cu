@@ -1,9 +1,10 @@
 // Decompression cache of a handle: per tensor (column j, component k)
 //   W_j[i3][i2][a] = sum_{b,c} G_j[a,b,c] U2_j[i2,b] U3_j[i3,c]     (= G x2 U2 x3 U3, Eq. Tucker)
-//   U1_j row-major [i1][a] with row stride r1 rounded up to 2 (16-byte aligned rows)
-// Both depend only on the compressed data, so they are computed once (first product call) and
-// reused by every product; the last mode product with U1 stays in the product kernels.
-// Size: sum over tensors of (n2 n3 r1 + n1 r1p) complex64.
+//   U1_j blocked by i1 tiles: [t1][a][i1 - t1 B1], row stride B1p
+// with a < r1p (r1 rounded up to 2) and zero padding, so that the per-tile blocks are 16-byte
+// aligned contiguous runs.  Both depend only on the compressed data, so they are computed once
+// (first product call) and reused by every product; the last mode product with U1 stays in the
+// product kernels.  Size: sum over tensors of (n2 n3 + nb1 B1p) r1p complex64.
 #include <algorithm>
 
 #include "decomp.cuh"
@@ -35,11 +36,12 @@ __global__ void __launch_bounds__(256) build_w_kernel(const float2* __restrict__
     Ps[o] = acc;  // o = a + r1 * b
   }
   __syncthreads();
-  float2* W = cache + cd.woff + (int64_t)i3 * n2 * d.r1;
-  for (int o = threadIdx.x; o < n2 * d.r1; o += blockDim.x) {
-    const int a = o % d.r1, i2 = o / d.r1;
+  float2* W = cache + cd.woff + (int64_t)i3 * n2 * cd.r1p;
+  for (int o = threadIdx.x; o < n2 * cd.r1p; o += blockDim.x) {
+    const int a = o % cd.r1p, i2 = o / cd.r1p;
     float2 acc = make_float2(0.f, 0.f);
-    for (int b = 0; b < d.r2; ++b) acc = cfma(Ps[a + d.r1 * b], U2[i2 + (int64_t)n2 * b], acc);
+    if (a < d.r1)
+      for (int b = 0; b < d.r2; ++b) acc = cfma(Ps[a + d.r1 * b], U2[i2 + (int64_t)n2 * b], acc);
     W[o] = acc;
   }
 }
@@ -51,9 +53,13 @@ __global__ void __launch_bounds__(256) build_u1_kernel(const float2* __restrict_
   const TensorDesc d = desc[t];
   const CacheDesc cd = cdesc[t];
   const float2* U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n1 * cd.r1p; o += gridDim.x * blockDim.x) {
-    const int a = o % cd.r1p, i1 = o / cd.r1p;
-    cache[cd.uoff + o] = a < d.r1 ? U1[i1 + (int64_t)n1 * a] : make_float2(0.f, 0.f);
+  const int B1 = tile_b1(n1), B1p = tile_b1p(n1), nb1 = (n1 + B1 - 1) / B1;
+  const int per = cd.r1p * B1p;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nb1 * per; o += gridDim.x * blockDim.x) {
+    const int t1 = o / per, rem = o % per;
+    const int a = rem / B1p, il = rem % B1p;
+    const int i1 = t1 * B1 + il;
+    cache[cd.uoff + o] = (a < d.r1 && il < B1 && i1 < n1) ? U1[i1 + (int64_t)n1 * a] : make_float2(0.f, 0.f);
   }
 }
 
@@ -63,15 +69,15 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
   std::vector<CacheDesc> cd(T);
   int64_t off = 0;
   int rmax = 0, r2max = 0;
+  const int nb1 = (h.n1 + tile_b1(h.n1) - 1) / tile_b1(h.n1);
   for (int t = 0; t < T; ++t) {
     const TensorDesc& d = h.desc[t];
     cd[t].r1 = d.r1;
     cd[t].r1p = (d.r1 + 1) / 2 * 2;
     cd[t].woff = off;
-    off += (int64_t)h.n2 * h.n3 * d.r1;
-    off = (off + 1) / 2 * 2;
+    off += (int64_t)h.n2 * h.n3 * cd[t].r1p;
     cd[t].uoff = off;
-    off += (int64_t)h.n1 * cd[t].r1p;
+    off += (int64_t)nb1 * tile_b1p(h.n1) * cd[t].r1p;
     rmax = std::max(rmax, cd[t].r1p);
     r2max = std::max(r2max, d.r1 * d.r2);
   }
@@ -79,6 +85,9 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
     set_error("product kernels support ranks r1 <= %d (handle has %d)", kRmax, rmax);
     return ZBC_EINVAL;
   }
+  // the error word of the product kernels lives as long as the cache (no allocation later)
+  ZBC_TRY(h.work_err.ensure(sizeof(int)));
+  ZBC_TRY_CUDA(cudaMemsetAsync(h.work_err.ptr, 0, sizeof(int), st));
   auto* c = new DecompCache();
   c->elems = off;
   cudaError_t e = cudaMalloc(&c->data, sizeof(float2) * std::max<int64_t>(1, off));
@@ -93,7 +102,7 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
   for (int t0 = 0; t0 < T; t0 += 65535) {
     const int nt = std::min(65535, T - t0);
     build_w_kernel<<<dim3(h.n3, nt), 256, sm, st>>>(h.d_pool, h.d_desc + t0, c->d_desc + t0, h.n1, h.n2, h.n3, c->data);
-    build_u1_kernel<<<dim3(ceil_div((int64_t)h.n1 * rmax, 256), nt), 256, 0, st>>>(h.d_pool, h.d_desc + t0, c->d_desc + t0,
+    build_u1_kernel<<<dim3(ceil_div((int64_t)nb1 * tile_b1p(h.n1) * rmax, 256), nt), 256, 0, st>>>(h.d_pool, h.d_desc + t0, c->d_desc + t0,
                                                                                 h.n1, c->data);
     count_launch(2);
   }

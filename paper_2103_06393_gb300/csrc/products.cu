@@ -58,3 +58,17 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   if (h.has_v) return aca_post(h, out, p, (float2*)Psi, ldpsi, stream);
   return ZBC_OK;
 }
+
+extern "C" int zbc_product_status(const zbc_handle* hh, zbc_stream stream) {
+  clear_error();
+  ZBC_CHECK_ARG(hh, "zbc_product_status: null handle");
+  Handle& h = const_cast<zbc_handle*>(hh)->h;
+  ZBC_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (!h.work_err.ptr) return ZBC_OK;  // no product has run yet
+  int flag = 0;
+  ZBC_TRY_CUDA(cudaMemcpy(&flag, h.work_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return ZBC_OK;
+  ZBC_TRY_CUDA(cudaMemset(h.work_err.ptr, 0, sizeof(int)));
+  set_error("a product kernel gave up a bounded device wait; its output is incomplete");
+  return ZBC_ETIMEOUT;
+}

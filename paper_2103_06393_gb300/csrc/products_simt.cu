@@ -2,83 +2,20 @@
 // cores (Sec. III.B), plus the ACA pre/post products X' = V^H X and Psi = V Psi'.
 //
 // The decompressed column never reaches HBM: a CTA decompresses its voxel tile column by
-// column (chunked front end in decomp.cuh) and either accumulates Y^k[v,s] += Z[v,j] X[j,s]
-// in registers (Algorithm 1) or reduces sum_v conj(Z[v,j]) Phi^k[v,s] over the tile
-// (Algorithm 2) into a per-CTA accumulator that a second kernel sums in a fixed order.
+// column and either accumulates Y^k[v,s] += Z[v,j] X[j,s] in registers (Algorithm 1) or
+// reduces sum_v conj(Z[v,j]) Phi^k[v,s] over the tile (Algorithm 2) into a per-CTA
+// accumulator that a second kernel sums in a fixed order.  The per-column inputs arrive through
+// the bulk-copy stage pipeline of stage.cuh: warps 0 .. ntask-1 compute (one task of 32 i1 x
+// kUQ i2 each), warp ntask copies (and, in Algorithm 2, sums the warps' per-column results).
 #include <algorithm>
 
-#include "decomp.cuh"
+#include "stage.cuh"
 
 namespace zbc {
 
-// ---------------------------------------------------------------------------------------------
-// Algorithm 1: one task (32 i1 x kUQ u) per warp
-// ---------------------------------------------------------------------------------------------
-template <int PS>
-__global__ void __launch_bounds__(kThreads, 1)
-    matvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
-                       int R, const float2* __restrict__ X, int64_t ldx, int p, float2* __restrict__ Y,
-                       int64_t ldy) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  // two front-end buffers (chunk c uses buffer c & 1), so one barrier per chunk suffices
-  const FrontEnd2 fe(smem, R, g.NUp, kChunk * PS);
-  const int k = blockIdx.y;
-  const int s0 = blockIdx.z * PS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  int i1_0, i2_0, i3;
-  g.tile(blockIdx.x, i1_0, i2_0, i3);
-  const bool active = warp < g.ntask;
-  int i1 = 0, u0 = 0;
-  bool ok = false;
-  if (active) g.task(i1_0, warp, lane, i1, u0, ok);
-  float2 acc[kUQ][PS];
-#pragma unroll
-  for (int l = 0; l < kUQ; ++l)
-#pragma unroll
-    for (int i = 0; i < PS; ++i) acc[l][i] = make_float2(0.f, 0.f);
-  WPrefetch pf;
-  pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3, tid, nthr);
-  for (int j0 = 0, c = 0; j0 < M; j0 += kChunk, ++c) {
-    const int jc = min(kChunk, M - j0);
-    const int b = c & 1;
-    const ChunkSmem cs = fe.cs(b);
-    float2* xs = fe.xs(b);
-    for (int e = tid; e < jc * PS; e += nthr) {
-      const int jj = e / PS, i = e % PS;
-      xs[e] = (s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
-    }
-    pf.store(cs, g, R, jc, tid, nthr);
-    __syncthreads();
-    if (j0 + kChunk < M)
-      pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3, tid, nthr);
-    if (active) {
-      for (int jj = 0; jj < jc; ++jj) {
-        const CacheDesc d = cs.cd[jj];
-        float2 z[kUQ];
-        last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok, cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, z);
-#pragma unroll
-        for (int i = 0; i < PS; ++i) {
-          const float2 x = xs[jj * PS + i];
-#pragma unroll
-          for (int l = 0; l < kUQ; ++l) acc[l][i] = cfma(z[l], x, acc[l][i]);
-        }
-      }
-    }
-  }
-  if (!active || !ok) return;
-  const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
-#pragma unroll
-  for (int l = 0; l < kUQ; ++l) {
-    const int i2 = i2_0 + u0 + l;
-    if (u0 + l >= g.NU || i2 >= g.n2) continue;
-    const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
-    float2* y = Y + k * nv + v;
-#pragma unroll
-    for (int i = 0; i < PS; ++i)
-      if (s0 + i < p) y[ldy * (s0 + i)] = acc[l][i];
-  }
-}
+constexpr int kSimtTasks = 9;                       // consumer warps per CTA at most
+constexpr int kSimtThreads = 32 * (kSimtTasks + 1);  // + the producer warp
+constexpr size_t kSmemBudget = 220 * 1024;
 
 // ---------------------------------------------------------------------------------------------
 // warp reduce-scatter of NV floats per lane: afterwards lane l holds the warp sum of value index
@@ -111,90 +48,278 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
   return r;
 }
 
+// X^T[j][s] = X[j, s] for s < p, zero up to the row stride pst (a whole number of s-chunks)
+__global__ void __launch_bounds__(256) transpose_x_kernel(const float2* __restrict__ X, int64_t ldx, int M, int p,
+                                                          int pst, float2* __restrict__ XT) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * pst) return;
+  const int j = (int)(e / pst), s = (int)(e % pst);
+  XT[e] = s < p ? X[j + ldx * s] : make_float2(0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------------------------
-// Algorithm 2: per-CTA partial sums over its tiles, partial[(cta*q+k)][s][j] (M x p)
+// Algorithm 1: one CTA per (voxel tile, component k, s-chunk); items = the M stored columns
 // ---------------------------------------------------------------------------------------------
 template <int PS>
-__global__ void __launch_bounds__(kThreads, 1)
-    rmatvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
-                        int R, int MJ, const float2* __restrict__ Phi, int64_t ldphi, int p,
-                        float2* __restrict__ partial) {
-  constexpr int NV = 2 * PS;
-  constexpr int SH = 5 - Log2<NV>::v;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int nw = blockDim.x >> 5;
-  const FrontEnd2 fe(smem, R, g.NUp, 0);   // chunk c uses buffer c & 1
-  float* red = (float*)fe.end();            // [kChunk][nw][NV]
-  float* pacc = red + kChunk * nw * NV;     // [MJ][NV]
-  const int k = blockIdx.y % q;
-  const int jb0 = (blockIdx.y / q) * MJ;
-  const int jb1 = min(M, jb0 + MJ);
+__global__ void __launch_bounds__(kSimtThreads, 1)
+    matvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
+                       StageLayout SL, int S, const float2* __restrict__ XT, int pst, int p,
+                       float2* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ int meta[kMaxStages];
+  __shared__ volatile int abort_flag;
+  const int k = blockIdx.y;
   const int s0 = blockIdx.z * PS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
-  const bool active = warp < g.ntask;
-  for (int e = threadIdx.x; e < (jb1 - jb0) * NV; e += blockDim.x) pacc[e] = 0.f;
-  int c = 0;
-  for (int t = blockIdx.x; t < g.ntiles(); t += gridDim.x) {
-    int i1_0, i2_0, i3;
-    g.tile(t, i1_0, i2_0, i3);
-    int i1 = 0, u0 = 0;
-    bool ok = false;
-    if (active) g.task(i1_0, warp, lane, i1, u0, ok);
-    float2 ph[kUQ][PS];
-#pragma unroll
-    for (int l = 0; l < kUQ; ++l) {
-      const int i2 = i2_0 + u0 + l;
-      const bool okl = ok && (u0 + l) < g.NU && i2 < g.n2;
-      const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
-#pragma unroll
-      for (int i = 0; i < PS; ++i)
-        ph[l][i] = (okl && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
+  const int ncw = g.ntask;
+  const int B1p = (g.B1 + 1) / 2 * 2;
+  int i1_0, i2_0, i3;
+  g.tile(blockIdx.x, i1_0, i2_0, i3);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], ncw);
     }
-    WPrefetch pf;
-    pf.load(cache, cdesc, g, R, q, k, jb0, min(kChunk, jb1 - jb0), i2_0, i3, tid, nthr);
-    for (int j0 = jb0; j0 < jb1; j0 += kChunk, ++c) {
-      const int jc = min(kChunk, jb1 - j0);
-      const ChunkSmem cs = fe.cs(c & 1);
-      pf.store(cs, g, R, jc, tid, nthr);
-      __syncthreads();
-      if (j0 + kChunk < jb1)
-        pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, jb1 - j0 - kChunk), i2_0, i3, tid, nthr);
-      for (int jj = 0; jj < jc; ++jj) {
-        const CacheDesc d = cs.cd[jj];
-        float2 z[kUQ];
-        last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok && active, cs.W + (size_t)jj * R * g.NUp, g.NUp,
-                   u0, z);
-        float vals[NV];
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  if (warp == ncw) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      const uint32_t xb = StageLayout::r16(8u * PS);
+      int issued = 0;
+      for (int c = 0; c < M; ++c) {
+        const int st = c % S;
+        if (c >= S && (abort_flag || !tc::mbar_wait(&empty[st], ((c / S) - 1) & 1))) {
+          abort_flag = 1;
+          break;
+        }
+        const CacheDesc d = cdesc[(int64_t)c * q + k];
+        issue_item(smem + (size_t)st * SL.stride, SL, &full[st], &meta[st], cache, d, g, B1p, i1_0, i2_0, i3,
+                   XT + (int64_t)c * pst + s0, xb);
+        issued = c + 1;
+      }
+      if (abort_flag)  // let the copies in flight land before the CTA exits
+        for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&full[c % S], (c / S) & 1);
+    }
+  } else {
+    // ---------------- consumers ----------------
+    int i1, u0;
+    bool ok;
+    g.task(i1_0, warp, lane, i1, u0, ok);
+    const int il = ok ? i1 - i1_0 : 0;
+    float2 acc[kUQ][PS];
 #pragma unroll
-        for (int i = 0; i < PS; ++i) {
-          float re = 0.f, im = 0.f;
+    for (int l = 0; l < kUQ; ++l)
+#pragma unroll
+      for (int i = 0; i < PS; ++i) acc[l][i] = make_float2(0.f, 0.f);
+    for (int c = 0; c < M; ++c) {
+      const int st = c % S;
+      // warp-uniform decisions: the warp shuffles below need every lane
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], (c / S) & 1))) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      const unsigned char* sb = smem + (size_t)st * SL.stride;
+      float2 z[kUQ];
+      last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0, z);
+      if constexpr (PS == 1) {
+        const float2 x = *(const float2*)(sb + SL.x);
+#pragma unroll
+        for (int l = 0; l < kUQ; ++l) acc[l][0] = cfma(z[l], x, acc[l][0]);
+      } else {
+        const float4* xs = (const float4*)(sb + SL.x);
+#pragma unroll
+        for (int i = 0; i < PS / 2; ++i) {
+          const float4 x = xs[i];
 #pragma unroll
           for (int l = 0; l < kUQ; ++l) {
-            re = fmaf(z[l].x, ph[l][i].x, fmaf(z[l].y, ph[l][i].y, re));
-            im = fmaf(z[l].x, ph[l][i].y, fmaf(-z[l].y, ph[l][i].x, im));
+            acc[l][2 * i] = cfma(z[l], make_float2(x.x, x.y), acc[l][2 * i]);
+            acc[l][2 * i + 1] = cfma(z[l], make_float2(x.z, x.w), acc[l][2 * i + 1]);
           }
-          vals[2 * i] = re;
-          vals[2 * i + 1] = im;
         }
-        const float r = warp_reduce_scatter<NV>(vals, lane);
-        if ((lane & ((1 << SH) - 1)) == 0) red[(jj * nw + warp) * NV + (lane >> SH)] = r;
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < jc * NV; e += blockDim.x) {
-        const int jj = e / NV, i = e % NV;
-        float tsum = 0.f;
-        for (int w = 0; w < nw; ++w) tsum += red[(jj * nw + w) * NV + i];
-        pacc[(j0 + jj - jb0) * NV + i] += tsum;
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&empty[st]);
+    }
+    if (ok && !abort_flag) {
+      const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
+#pragma unroll
+      for (int l = 0; l < kUQ; ++l) {
+        const int i2 = i2_0 + u0 + l;
+        if (u0 + l >= g.NU || i2 >= g.n2) continue;
+        const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
+        float2* y = Y + k * nv + v;
+#pragma unroll
+        for (int i = 0; i < PS; ++i)
+          if (s0 + i < p) y[ldy * (s0 + i)] = acc[l][i];
       }
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Algorithm 2: grid (G, q * jblocks, s-chunks).  The (tile, column) items of one j-block are
+// split into G equal contiguous ranges, one per CTA; a CTA's partial sums go to
+// partial[(cta * q + k)][s][j] (M x p), summed over the G CTAs by reduce_partials_kernel.
+// Per item, each consumer warp reduces its voxels' sum_v conj(Z[v,j]) Phi[v,s] with a warp
+// reduce-scatter into the stage's red[warp][NV]; the producer warp adds the warps' values in
+// warp order into pacc[j][NV] (fixed order: results are reproducible) before it reuses the stage.
+// ---------------------------------------------------------------------------------------------
+template <int PS>
+__global__ void __launch_bounds__(kSimtThreads, 1)
+    rmatvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
+                        int MJ, StageLayout SL, int S, const float2* __restrict__ Phi, int64_t ldphi, int p,
+                        float2* __restrict__ partial, int* __restrict__ err) {
+  constexpr int NV = 2 * PS;
+  constexpr int SH = 5 - Log2<NV>::v;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ int meta[kMaxStages];
+  __shared__ volatile int abort_flag;
+  float* pacc = (float*)(smem + (size_t)S * SL.stride);  // [MJ][NV]
+  const int k = blockIdx.y % q;
+  const int jb0 = (blockIdx.y / q) * MJ;
+  const int nj = min(M, jb0 + MJ) - jb0;
+  const int s0 = blockIdx.z * PS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncw = g.ntask;
+  const int B1p = (g.B1 + 1) / 2 * 2;
+  const int64_t N = (int64_t)g.ntiles() * nj;
+  const int64_t c0 = N * blockIdx.x / gridDim.x;
+  const int nitems = (int)(N * (blockIdx.x + 1) / gridDim.x - c0);
+  for (int e = threadIdx.x; e < nj * NV; e += blockDim.x) pacc[e] = 0.f;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], ncw);
+    }
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  if (warp == ncw) {
+    // ---------------- producer and reducer ----------------
+    // item c (local) -> global index c0 + c -> (tile (c0 + c) / nj, column jb0 + (c0 + c) % nj)
+    auto reduce = [&](int c) {
+      const int jl = (int)((c0 + c) % nj);
+      const float* red = (const float*)(smem + (size_t)(c % S) * SL.stride + SL.red);
+      if (lane < NV) {
+        float sum = 0.f;
+        for (int w = 0; w < ncw; ++w) sum += red[w * NV + lane];
+        pacc[jl * NV + lane] += sum;
+      }
+    };
+    int t = (int)(c0 / (nj > 0 ? nj : 1)), jl = (int)(c0 % (nj > 0 ? nj : 1));
+    int issued = 0;
+    for (int c = 0; c < nitems; ++c) {
+      const int st = c % S;
+      if (c >= S) {
+        bool bad = abort_flag != 0;
+        if (!bad) bad = !tc::mbar_wait(&empty[st], ((c / S) - 1) & 1);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        reduce(c - S);
+        __syncwarp();
+      }
+      if (lane == 0) {
+        int i1_0, i2_0, i3;
+        g.tile(t, i1_0, i2_0, i3);
+        const CacheDesc d = cdesc[(int64_t)(jb0 + jl) * q + k];
+        issue_item(smem + (size_t)st * SL.stride, SL, &full[st], &meta[st], cache, d, g, B1p, i1_0, i2_0, i3,
+                   nullptr, 0u);
+      }
+      issued = c + 1;
+      if (++jl == nj) {
+        jl = 0;
+        ++t;
+      }
+    }
+    if (!__any_sync(0xffffffffu, abort_flag != 0)) {
+      for (int c = std::max(0, nitems - S); c < nitems; ++c) {
+        bool bad = abort_flag != 0;
+        if (!bad) bad = !tc::mbar_wait(&empty[c % S], (c / S) & 1);
+        if (__any_sync(0xffffffffu, bad)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        reduce(c);
+      }
+    }
+    if (abort_flag && lane == 0)  // let the copies in flight land before the CTA exits
+      for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&full[c % S], (c / S) & 1);
+  } else {
+    // ---------------- consumers ----------------
+    const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
+    int t = (int)(c0 / (nj > 0 ? nj : 1)), jl = (int)(c0 % (nj > 0 ? nj : 1));
+    int tcur = -1, il = 0, u0 = 0;
+    bool okl[kUQ];
+    float2 ph[kUQ][PS];
+    for (int c = 0; c < nitems; ++c) {
+      const int st = c % S;
+      if (t != tcur) {
+        // the task's Phi values on this tile (zero outside the grid)
+        tcur = t;
+        int i1_0, i2_0, i3, i1;
+        bool ok;
+        g.tile(t, i1_0, i2_0, i3);
+        g.task(i1_0, warp, lane, i1, u0, ok);
+        il = ok ? i1 - i1_0 : 0;
+#pragma unroll
+        for (int l = 0; l < kUQ; ++l) {
+          const int i2 = i2_0 + u0 + l;
+          okl[l] = ok && (u0 + l) < g.NU && i2 < g.n2;
+          const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
+#pragma unroll
+          for (int i = 0; i < PS; ++i)
+            ph[l][i] = (okl[l] && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
+        }
+      }
+      if (++jl == nj) {
+        jl = 0;
+        ++t;
+      }
+      // warp-uniform decisions: the warp shuffles below need every lane
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], (c / S) & 1))) {
+        if (lane == 0) abort_flag = 1;
+        break;
+      }
+      unsigned char* sb = smem + (size_t)st * SL.stride;
+      float2 z[kUQ];
+      last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0, z);
+      float vals[NV];
+#pragma unroll
+      for (int i = 0; i < PS; ++i) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int l = 0; l < kUQ; ++l) {
+          const float2 zz = okl[l] ? z[l] : make_float2(0.f, 0.f);
+          re = fmaf(zz.x, ph[l][i].x, fmaf(zz.y, ph[l][i].y, re));
+          im = fmaf(zz.x, ph[l][i].y, fmaf(-zz.y, ph[l][i].x, im));
+        }
+        vals[2 * i] = re;
+        vals[2 * i + 1] = im;
+      }
+      const float r = warp_reduce_scatter<NV>(vals, lane);
+      if ((lane & ((1 << SH) - 1)) == 0) ((float*)(sb + SL.red))[warp * NV + (lane >> SH)] = r;
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&empty[st]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
   float2* out = partial + (int64_t)(blockIdx.x * q + k) * M * p;
-  for (int e = threadIdx.x; e < (jb1 - jb0) * PS; e += blockDim.x) {
-    const int jl = e % (jb1 - jb0), i = e / (jb1 - jb0);
-    if (s0 + i < p) out[(jb0 + jl) + (int64_t)M * (s0 + i)] = make_float2(pacc[jl * NV + 2 * i], pacc[jl * NV + 2 * i + 1]);
+  for (int e = threadIdx.x; e < nj * PS; e += blockDim.x) {
+    const int j = e % nj, i = e / nj;
+    if (s0 + i < p) out[(jb0 + j) + (int64_t)M * (s0 + i)] = make_float2(pacc[j * NV + 2 * i], pacc[j * NV + 2 * i + 1]);
   }
 }
 
@@ -246,6 +371,8 @@ int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ld
   return ZBC_OK;
 }
 
+
+
 int reduce_partials(const float2* partial, int ng, int M, int p, float2* out, int64_t ldo, cudaStream_t st) {
   reduce_partials_kernel<<<ceil_div((int64_t)M * p, 256), 256, 0, st>>>(partial, ng, M, p, out, ldo);
   ZBC_TRY_CUDA(cudaGetLastError());
@@ -253,88 +380,82 @@ int reduce_partials(const float2* partial, int ng, int M, int p, float2* out, in
   return ZBC_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
 template <int PS>
 static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
   ZBC_TRY(build_decomp_cache(h, st));
+  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, kSimtTasks);
   const int R = h.cache_r;
-  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
-  const int nthr = 32 * std::max(4, g.ntask);
-  const size_t sm = 2 * FrontEnd2::buf_bytes(R, g.NUp, kChunk * PS);
+  const int B1p = tile_b1p(h.n1);
+  const int schunks = ceil_div(p, PS);
+  const int pst = (schunks * PS + 1) / 2 * 2;
+  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (size_t)h.M * pst));
+  float2* XT = (float2*)h.work_xt.ptr;
+  transpose_x_kernel<<<ceil_div((int64_t)h.M * pst, 256), 256, 0, st>>>(X, ldx, h.M, p, pst, XT);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  const StageLayout SL = StageLayout::make(R, B1p, g.NUp, 8 * PS, 0);
+  const int S = (int)std::min<size_t>(kMaxStages, kSmemBudget / SL.stride);
+  ZBC_CHECK_ARG(S >= 2, "rank %d too large for the FP32 SIMT path", R);
+  const size_t sm = (size_t)S * SL.stride;
   static bool attr_set = false;
   if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmemBudget));
     attr_set = true;
   }
-  ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT path", R);
-  dim3 grid(g.ntiles(), h.q, ceil_div(p, PS));
-  matvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, X, ldx, p, Y,
-                                                     ldy);
+  dim3 grid(g.ntiles(), h.q, schunks);
+  matvec_simt_kernel<PS><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL, S,
+                                                               XT, pst, p, Y, ldy, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;
 }
 
+// Algorithm 2 with the partial sums in `scratch` (scratch_bytes) or, when scratch is null, in
+// the handle's workspace (grown as needed).
 template <int PS>
 static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
-                          cudaStream_t st) {
-  ZBC_TRY(build_decomp_cache(h, st));
+                          float2* scratch, size_t scratch_bytes, cudaStream_t st) {
+  if (!scratch) ZBC_TRY(build_decomp_cache(h, st));
+  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, kSimtTasks);
   const int R = h.cache_r;
-  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
-  const int NV = 2 * PS;
-  const int nthr = 32 * std::max(4, g.ntask);
-  const size_t base = 2 * FrontEnd2::buf_bytes(R, g.NUp, 0) + sizeof(float) * kChunk * (nthr / 32) * NV;
-  // j-block so that the per-CTA accumulator stays within the shared-memory budget
-  const size_t budget = 220 * 1024 - base;
-  const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
-  const int jblocks = ceil_div(h.M, MJ);
-  const int schunks = ceil_div(p, PS);
-  const int target = 2 * sm_count();
-  int G = std::max(1, target / std::max(1, h.q * jblocks * schunks));
-  G = std::min(G, g.ntiles());
-  const size_t sm = base + sizeof(float) * (size_t)MJ * NV;
-  static bool attr_set = false;
-  if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
-  ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT adjoint", R);
-  ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)G * h.q * h.M * p));
-  float2* partial = (float2*)h.work_partial.ptr;
-  dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
-                                                  p, partial);
-  ZBC_TRY_CUDA(cudaGetLastError());
-  count_launch();
-  return reduce_partials(partial, G * h.q, h.M, p, out, ldo, st);
-}
-
-// The same adjoint with caller-provided scratch for the partial sums and no allocation at all:
-// the decompression cache must already exist, and the number of partial-sum groups is capped
-// so that they fit scratch_bytes.
-template <int PS>
-static int launch_rmatvec_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
-                                  float2* scratch, size_t scratch_bytes, cudaStream_t st) {
-  const int R = h.cache_r;
-  Geo g = make_geo(h.n1, h.n2, h.n3, R, 8);
-  const int NV = 2 * PS;
-  const int nthr = 32 * std::max(4, g.ntask);
-  const size_t base = 2 * FrontEnd2::buf_bytes(R, g.NUp, 0) + sizeof(float) * kChunk * (nthr / 32) * NV;
-  const size_t budget = 220 * 1024 - base;
-  const int MJ = std::max(kChunk, std::min(h.M, (int)(budget / (NV * sizeof(float))) / kChunk * kChunk));
+  const int B1p = tile_b1p(h.n1);
+  constexpr int NV = 2 * PS;
+  const StageLayout SL = StageLayout::make(R, B1p, g.NUp, 0, 4 * NV * g.ntask);
+  // stages first (4, or as many as fit), the rest of shared memory holds the j-block's sums
+  const int S = (int)std::min<size_t>(4, kSmemBudget / SL.stride);
+  ZBC_CHECK_ARG(S >= 2, "rank %d too large for the FP32 SIMT adjoint", R);
+  const size_t left = kSmemBudget - (size_t)S * SL.stride;
+  const int MJ = (int)std::min<size_t>(h.M, left / (sizeof(float) * NV));
+  ZBC_CHECK_ARG(MJ >= 1, "rank %d too large for the FP32 SIMT adjoint", R);
   const int jblocks = ceil_div(h.M, MJ);
   const int schunks = ceil_div(p, PS);
   const size_t per_group = sizeof(float2) * (size_t)h.q * h.M * p;
-  const int gmax = (int)std::min<size_t>(scratch_bytes / per_group, 1 << 20);
-  ZBC_CHECK_ARG(gmax >= 1, "scratch of %zu bytes cannot hold one partial-sum group (%zu bytes)", scratch_bytes,
-                per_group);
-  int G = std::max(1, 2 * sm_count() / std::max(1, h.q * jblocks * schunks));
-  G = std::min(std::min(G, g.ntiles()), gmax);
-  const size_t sm = base + sizeof(float) * (size_t)MJ * NV;
-  ZBC_CHECK_ARG(sm <= 220 * 1024, "rank %d too large for the FP32 SIMT adjoint", R);
-  ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  int G = std::max(1, sm_count() / std::max(1, h.q * jblocks * schunks));
+  G = std::min(G, std::max(1, g.ntiles()));
+  if (scratch) {
+    const size_t gmax = scratch_bytes / per_group;
+    ZBC_CHECK_ARG(gmax >= 1, "scratch of %zu bytes cannot hold one partial-sum group (%zu bytes)", scratch_bytes,
+                  per_group);
+    G = (int)std::min<size_t>(G, gmax);
+  } else {
+    ZBC_TRY(h.work_partial.ensure(per_group * G));
+    scratch = (float2*)h.work_partial.ptr;
+  }
+  const size_t sm = (size_t)S * SL.stride + sizeof(float) * (size_t)MJ * NV;
+  static bool attr_set = false;
+  if (!attr_set) {
+    ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmemBudget));
+    attr_set = true;
+  }
   dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, nthr, sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, MJ, Phi, ldphi,
-                                                  p, scratch);
+  rmatvec_simt_kernel<PS><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, MJ, SL,
+                                                                S, Phi, ldphi, p, scratch, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);
@@ -346,11 +467,11 @@ int rmatvec_simt_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, flo
     set_error("the handle's decompression cache is not built: call zbc_matvec or zbc_rmatvec on it once first");
     return ZBC_EINVAL;
   }
-  if (p == 1) return launch_rmatvec_scratch<1>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p == 2) return launch_rmatvec_scratch<2>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p <= 4) return launch_rmatvec_scratch<4>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p <= 8) return launch_rmatvec_scratch<8>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  return launch_rmatvec_scratch<16>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p == 1) return launch_rmatvec<1>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p == 2) return launch_rmatvec<2>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 4) return launch_rmatvec<4>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 8) return launch_rmatvec<8>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  return launch_rmatvec<16>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
 }
 
 int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
@@ -362,11 +483,11 @@ int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64
 }
 
 int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st) {
-  if (p == 1) return launch_rmatvec<1>(h, Phi, ldphi, p, out, ldo, st);
-  if (p == 2) return launch_rmatvec<2>(h, Phi, ldphi, p, out, ldo, st);
-  if (p <= 4) return launch_rmatvec<4>(h, Phi, ldphi, p, out, ldo, st);
-  if (p <= 8) return launch_rmatvec<8>(h, Phi, ldphi, p, out, ldo, st);
-  return launch_rmatvec<16>(h, Phi, ldphi, p, out, ldo, st);
+  if (p == 1) return launch_rmatvec<1>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  if (p == 2) return launch_rmatvec<2>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  if (p <= 4) return launch_rmatvec<4>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  if (p <= 8) return launch_rmatvec<8>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  return launch_rmatvec<16>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
 }
 
 }  // namespace zbc

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int s0 = blockIdx.z * P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nprod = L.nprodw * 32;
+  const int B1p = (g.B1 + 1) / 2 * 2;
   int i1_0, i2_0, i3;
   g.tile(blockIdx.x, i1_0, i2_0, i3);
 
@@ -264,8 +265,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             float2 zz[kUQ];
             if (jj < jc) {
               const CacheDesc d = cs.cd[jj];
-              last_mode4(cache + d.uoff + (int64_t)i1 * d.r1p, d.r1, ok, cs.W + (size_t)jj * R * g.NUp, g.NUp,
-                         u0, zz);
+              const int t1 = i1_0 / g.B1, il = ok ? i1 - i1_0 : 0;
+              last_mode4(cache + d.uoff + (int64_t)t1 * d.r1p * B1p + il, B1p, d.r1, ok,
+                         cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, zz);
             } else {
 #pragma unroll
               for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
@@ -381,9 +383,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
     ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_tc_kernel<FMT, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 221 * 1024));
     attr_set = true;
   }
-  ZBC_TRY(h.work_misc.ensure(sizeof(int)));
-  int* err = (int*)h.work_misc.ptr;
-  ZBC_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  int* err = (int*)h.work_err.ptr;
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
   matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, L,
                                                                    X, ldx, p, Y, ldy, err);

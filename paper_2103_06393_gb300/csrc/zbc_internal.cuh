@@ -67,7 +67,7 @@ struct TensorDesc {
 };
 
 struct TcPack;       // tensor-core operand staging, built lazily (products_tc.cu)
-struct DecompCache;  // W = G x2 U2 x3 U3 and row-major U1 per tensor, built lazily (decomp_cache.cu)
+struct DecompCache;  // W = G x2 U2 x3 U3 and tile-blocked U1 per tensor, built lazily (decomp_cache.cu)
 void cache_release(DecompCache* c);
 
 struct Handle {
@@ -86,6 +86,8 @@ struct Handle {
   DevBuf work_partial;   // adjoint partial sums
   DevBuf work_x;         // X' = V^H X (ACA), scaled operands
   DevBuf work_misc;
+  DevBuf work_xt;        // X^T of the forward products (s-chunk padded rows)
+  DevBuf work_err;       // int: set by a product kernel whose bounded wait gave up
   TcPack* tc = nullptr;
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)

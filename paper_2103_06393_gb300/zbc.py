@@ -97,6 +97,7 @@ def lib():
             "zbc_mlp_train": ([vp, vp, vp, i32, i32, C.c_float, vp, vp], i32),
             "zbc_rank_widths": ([vp, vp, i32, C.POINTER(zbc_grid), i32, vp, vp], i32),
             "zbc_rmatvec_noalloc": ([vp, vp, i64, i32, vp, i64, vp], i32),
+            "zbc_product_status": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -398,6 +399,12 @@ def zbc_rmatvec_noalloc(h: Handle, Phi, Psi, stream=None):
     p = Phi.shape[0]
     _check(lib().zbc_rmatvec_noalloc(h.ptr, _ptr(Phi), _ld(Phi), p, _ptr(Psi), _ld(Psi), _stream(stream)))
     return Psi
+
+
+def zbc_product_status(h: Handle, stream=None):
+    """Synchronise the stream and raise ZbcError(ZBC_ETIMEOUT) if a product kernel of h gave up
+    a bounded device wait since the last check."""
+    _check(lib().zbc_product_status(h.ptr, _stream(stream)))
 
 
 def zbc_rmatvec(h: Handle, Phi, Psi, prec=FP32_SIMT, stream=None):

@@ -155,7 +155,7 @@ def _run(h, w, tens, p, prec, V=None, seed=0):
     Psi = zbc.colmajor(m, p, torch.complex64)
     zbc.zbc_matvec(h, zbc.to_colmajor(X), Y, prec)
     zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
-    torch.cuda.synchronize()
+    zbc.zbc_product_status(h)   # synchronises; raises if a kernel gave up a bounded wait
     if V is None:
         Yo = products.matvec(tens, g.shape, X)
         Po = products.rmatvec(tens, g.shape, Phi)
@@ -180,6 +180,46 @@ def test_simt_products_ragged_tiles(n):
     w = inputs.scaled_workload("precision", n, m=5)
     h, tens = _oracle_handle(w, 1e-5)
     Y, Yo, P, Po, _, _ = _run(h, w, tens, 5, zbc.FP32_SIMT, seed=3)
+    assert rel_cols(Y, Yo).max() < RTOL_FP32
+    assert rel_cols(P, Po).max() < RTOL_FP32
+
+
+@pytest.mark.parametrize("n", [(160, 7, 3), (257, 5, 2)])
+def test_simt_products_several_i1_tiles(n):
+    # n1 > 128: more than one i1 tile, the last one partly padding
+    w = inputs.scaled_workload("precision", n, m=6)
+    h, tens = _oracle_handle(w, 1e-5)
+    Y, Yo, P, Po, _, _ = _run(h, w, tens, 5, zbc.FP32_SIMT, seed=4)
+    assert rel_cols(Y, Yo).max() < RTOL_FP32
+    assert rel_cols(P, Po).max() < RTOL_FP32
+
+
+def _random_tensors(n, M, seed, rmax=7):
+    """M columns x 3 components of random Tucker tensors with ranks 1..rmax (odd and even),
+    orthonormal factors, complex64-exact."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(M):
+        tj = []
+        for _k in range(3):
+            r = [int(rng.integers(1, min(rmax, ni) + 1)) for ni in n]
+            G = rng.normal(size=r) + 1j * rng.normal(size=r)
+            Us = [np.linalg.qr(rng.normal(size=(ni, ri)) + 1j * rng.normal(size=(ni, ri)))[0]
+                  for ni, ri in zip(n, r)]
+            tj.append((G, Us))
+        out.append(tj)
+    return c64(out)
+
+
+def test_simt_products_many_columns():
+    # 2500 stored columns: many turns of the copy pipeline's stages, and more columns than one
+    # adjoint CTA keeps sums for (the j range is split into blocks)
+    n = (8, 6, 5)
+    tens = _random_tensors(n, 2500, seed=11)
+    grid = inputs.Grid(*n, 0.002)
+    h = zbc.zbc_create_from_host(grid, 3, tens)
+    w = inputs.Workload("random", grid, None, 0.0, 0.0, 16)
+    Y, Yo, P, Po, _, _ = _run(h, w, tens, 16, zbc.FP32_SIMT, seed=5)
     assert rel_cols(Y, Yo).max() < RTOL_FP32
     assert rel_cols(P, Po).max() < RTOL_FP32
 
