@@ -8,13 +8,14 @@
 // the bulk-copy stage pipeline of stage.cuh: warps 0 .. ntask-1 compute (one task of 32 i1 x
 // kUQ i2 each), warp ntask copies (and, in Algorithm 2, sums the warps' per-column results).
 #include <algorithm>
+#include <cstdlib>
 
 #include "stage.cuh"
 
 namespace zbc {
 
-constexpr int kSimtTasks = 9;                       // consumer warps per CTA at most
-constexpr int kSimtThreads = 32 * (kSimtTasks + 1);  // + the producer warp
+// NT = compute warps per CTA at most (template): 6 (8 warps with the copy warp, up to 255
+// registers per thread) or 9 (10 warps, 168 registers); see simt_warps()
 constexpr size_t kSmemBudget = 220 * 1024;
 
 // ---------------------------------------------------------------------------------------------
@@ -57,11 +58,23 @@ __global__ void __launch_bounds__(256) transpose_x_kernel(const float2* __restri
   XT[e] = s < p ? X[j + ldx * s] : make_float2(0.f, 0.f);
 }
 
+int transpose_rhs(Handle& h, const float2* X, int64_t ldx, int p, int chunk, const float2** XT, int* pst,
+                  cudaStream_t st) {
+  *pst = (ceil_div(p, chunk) * chunk + 1) / 2 * 2;
+  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (size_t)h.M * *pst));
+  float2* xt = (float2*)h.work_xt.ptr;
+  transpose_x_kernel<<<ceil_div((int64_t)h.M * *pst, 256), 256, 0, st>>>(X, ldx, h.M, p, *pst, xt);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  *XT = xt;
+  return ZBC_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Algorithm 1: one CTA per (voxel tile, component k, s-chunk); items = the M stored columns
 // ---------------------------------------------------------------------------------------------
-template <int PS>
-__global__ void __launch_bounds__(kSimtThreads, 1)
+template <int PS, int NT>
+__global__ void __launch_bounds__(32 * (NT + 1), 1)
     matvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                        StageLayout SL, int S, const float2* __restrict__ XT, int pst, int p,
                        float2* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
@@ -171,8 +184,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
 // reduce-scatter into the stage's red[warp][NV]; the producer warp adds the warps' values in
 // warp order into pacc[j][NV] (fixed order: results are reproducible) before it reuses the stage.
 // ---------------------------------------------------------------------------------------------
-template <int PS>
-__global__ void __launch_bounds__(kSimtThreads, 1)
+template <int PS, int NT>
+__global__ void __launch_bounds__(32 * (NT + 1), 1)
     rmatvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                         int MJ, StageLayout SL, int S, const float2* __restrict__ Phi, int64_t ldphi, int p,
                         float2* __restrict__ partial, int* __restrict__ err) {
@@ -384,31 +397,28 @@ int reduce_partials(const float2* partial, int ng, int M, int p, float2* out, in
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
-template <int PS>
+template <int PS, int NT>
 static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
   ZBC_TRY(build_decomp_cache(h, st));
-  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, kSimtTasks);
+  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, NT);
   const int R = h.cache_r;
   const int B1p = tile_b1p(h.n1);
   const int schunks = ceil_div(p, PS);
-  const int pst = (schunks * PS + 1) / 2 * 2;
-  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (size_t)h.M * pst));
-  float2* XT = (float2*)h.work_xt.ptr;
-  transpose_x_kernel<<<ceil_div((int64_t)h.M * pst, 256), 256, 0, st>>>(X, ldx, h.M, p, pst, XT);
-  ZBC_TRY_CUDA(cudaGetLastError());
-  count_launch();
+  const float2* XT;
+  int pst;
+  ZBC_TRY(transpose_rhs(h, X, ldx, p, PS, &XT, &pst, st));
   const StageLayout SL = StageLayout::make(R, B1p, g.NUp, 8 * PS, 0);
   const int S = (int)std::min<size_t>(kMaxStages, kSmemBudget / SL.stride);
   ZBC_CHECK_ARG(S >= 2, "rank %d too large for the FP32 SIMT path", R);
   const size_t sm = (size_t)S * SL.stride;
   static bool attr_set = false;
   if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSmemBudget));
     attr_set = true;
   }
   dim3 grid(g.ntiles(), h.q, schunks);
-  matvec_simt_kernel<PS><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL, S,
+  matvec_simt_kernel<PS, NT><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL, S,
                                                                XT, pst, p, Y, ldy, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
@@ -417,11 +427,11 @@ static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2*
 
 // Algorithm 2 with the partial sums in `scratch` (scratch_bytes) or, when scratch is null, in
 // the handle's workspace (grown as needed).
-template <int PS>
+template <int PS, int NT>
 static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
                           float2* scratch, size_t scratch_bytes, cudaStream_t st) {
   if (!scratch) ZBC_TRY(build_decomp_cache(h, st));
-  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, kSimtTasks);
+  const Geo g = make_geo(h.n1, h.n2, h.n3, 0, NT);
   const int R = h.cache_r;
   const int B1p = tile_b1p(h.n1);
   constexpr int NV = 2 * PS;
@@ -449,16 +459,46 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   const size_t sm = (size_t)S * SL.stride + sizeof(float) * (size_t)MJ * NV;
   static bool attr_set = false;
   if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSmemBudget));
     attr_set = true;
   }
   dim3 grid(G, h.q * jblocks, schunks);
-  rmatvec_simt_kernel<PS><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, MJ, SL,
+  rmatvec_simt_kernel<PS, NT><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, MJ, SL,
                                                                 S, Phi, ldphi, p, scratch, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);
+}
+
+// compute warps per CTA: the handle's tuned choice if any, else ZBC_SIMT_WARPS (6 or 9) from the
+// environment, else 9
+static int simt_warps(const Handle& h) {
+  if (h.simt_warps == 6 || h.simt_warps == 9) return h.simt_warps;
+  static int env = [] {
+    const char* e = getenv("ZBC_SIMT_WARPS");
+    return e ? atoi(e) : 0;
+  }();
+  return env == 6 ? 6 : 9;
+}
+
+template <int NT>
+static int rmatvec_dispatch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
+                            float2* scratch, size_t scratch_bytes, cudaStream_t st) {
+  if (p == 1) return launch_rmatvec<1, NT>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p == 2) return launch_rmatvec<2, NT>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 4) return launch_rmatvec<4, NT>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (p <= 8) return launch_rmatvec<8, NT>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  return launch_rmatvec<16, NT>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+}
+
+template <int NT>
+static int matvec_dispatch(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
+  if (p == 1) return launch_matvec<1, NT>(h, X, ldx, p, Y, ldy, st);
+  if (p == 2) return launch_matvec<2, NT>(h, X, ldx, p, Y, ldy, st);
+  if (p <= 4) return launch_matvec<4, NT>(h, X, ldx, p, Y, ldy, st);
+  if (p <= 8) return launch_matvec<8, NT>(h, X, ldx, p, Y, ldy, st);
+  return launch_matvec<16, NT>(h, X, ldx, p, Y, ldy, st);
 }
 
 int rmatvec_simt_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
@@ -467,27 +507,18 @@ int rmatvec_simt_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, flo
     set_error("the handle's decompression cache is not built: call zbc_matvec or zbc_rmatvec on it once first");
     return ZBC_EINVAL;
   }
-  if (p == 1) return launch_rmatvec<1>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p == 2) return launch_rmatvec<2>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p <= 4) return launch_rmatvec<4>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  if (p <= 8) return launch_rmatvec<8>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
-  return launch_rmatvec<16>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (simt_warps(h) == 6) return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  return rmatvec_dispatch<9>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
 }
 
 int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
-  if (p == 1) return launch_matvec<1>(h, X, ldx, p, Y, ldy, st);
-  if (p == 2) return launch_matvec<2>(h, X, ldx, p, Y, ldy, st);
-  if (p <= 4) return launch_matvec<4>(h, X, ldx, p, Y, ldy, st);
-  if (p <= 8) return launch_matvec<8>(h, X, ldx, p, Y, ldy, st);
-  return launch_matvec<16>(h, X, ldx, p, Y, ldy, st);
+  if (simt_warps(h) == 6) return matvec_dispatch<6>(h, X, ldx, p, Y, ldy, st);
+  return matvec_dispatch<9>(h, X, ldx, p, Y, ldy, st);
 }
 
 int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st) {
-  if (p == 1) return launch_rmatvec<1>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
-  if (p == 2) return launch_rmatvec<2>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
-  if (p <= 4) return launch_rmatvec<4>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
-  if (p <= 8) return launch_rmatvec<8>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
-  return launch_rmatvec<16>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  if (simt_warps(h) == 6) return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+  return rmatvec_dispatch<9>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
 }
 
 }  // namespace zbc

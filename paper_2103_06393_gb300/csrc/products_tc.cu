@@ -18,21 +18,24 @@
 // kFlush chunks and is added, with round-to-nearest FP32 on the CUDA cores, into a second TMEM
 // region S; Y = S + D at the end.
 //
-// Warp roles: the front-end ("producer") warps each own one task of the tile and fill the
-// operands of a chunk; one extra warp issues the MMAs.  Two operand buffers alternate; an
-// mbarrier "full" per buffer (one arrival per producer warp) hands a filled buffer to the
-// issuer, and tcgen05.commit on an mbarrier "empty" per buffer hands it back once the tensor
-// cores have consumed it.  Producers synchronise among themselves with a named barrier only.
+// Warp roles: a copy warp streams each column's U1 / W blocks into the stage ring of stage.cuh
+// (cp.async.bulk); the front-end ("producer") warps each own one task of the tile, form its
+// last mode product from the staged blocks and fill the operands of a chunk; one more warp
+// issues the MMAs.  Two operand buffers alternate; an mbarrier "full" per buffer (one arrival
+// per producer warp) hands a filled buffer to the issuer, and tcgen05.commit on an mbarrier
+// "empty" per buffer hands it back once the tensor cores have consumed it.  No CTA-wide barrier
+// is taken between the prologue and the epilogue.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
-#include "decomp.cuh"
-#include "tc_common.cuh"
+#include "stage.cuh"
 
 namespace zbc {
 
-constexpr int kFlush = 4;  // chunks accumulated in D before it is folded into S
+constexpr int kFlush = 4;       // chunks accumulated in D before it is folded into S
+constexpr int kTcMaxTasks = 8;  // producer warps with a task, at most
+constexpr int kTcThreads = 32 * (kTcMaxTasks + 2);  // + the copy warp and the MMA issuer
 
 struct TcPack {
   int dummy;
@@ -91,14 +94,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&w)[
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
-}
-
-__device__ __forceinline__ void bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 struct TcLayout {
   int NR;        // accumulator rows of the tile (multiple of 128)
   int nmt;       // M tiles
@@ -110,25 +105,25 @@ struct TcLayout {
 };
 
 template <int FMT, int P2>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     matvec_tc_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
-                     int R, TcLayout L, const float2* __restrict__ X, int64_t ldx, int p, float2* __restrict__ Y,
-                     int64_t ldy, int* __restrict__ err) {
+                     StageLayout SL, int S, TcLayout L, const float2* __restrict__ XT, int pst, int p,
+                     float2* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
   using F = Fmt<FMT>;
-  constexpr int P = P2 / 2;
   constexpr int NF = 16 / F::esz;  // floats per 16-byte chunk
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full[2], empty[2];
+  __shared__ uint64_t sfull[kMaxStages], sempty[kMaxStages], ofull[2], oempty[2];
+  __shared__ int meta[kMaxStages];
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_flag;
-  const FrontEnd2 fe(smem, R, g.NUp, kChunk * P);  // chunk c uses buffer c & 1
-  unsigned char* ops = (unsigned char*)(((uintptr_t)fe.end() + 1023) & ~(uintptr_t)1023);
+  unsigned char* stages = smem;
+  unsigned char* ops = (unsigned char*)(((uintptr_t)(smem + (size_t)S * SL.stride) + 1023) & ~(uintptr_t)1023);
   auto a_op = [&](int buf, int term) { return ops + (size_t)(buf * F::terms + term) * L.a_bytes; };
   auto b_op = [&](int buf, int term) {
     return ops + (size_t)2 * F::terms * L.a_bytes + (size_t)(buf * F::terms + term) * L.b_bytes;
   };
   const int k = blockIdx.y;
-  const int s0 = blockIdx.z * P;
+  const int s0 = blockIdx.z * (P2 / 2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nprod = L.nprodw * 32;
   const int B1p = (g.B1 + 1) / 2 * 2;
@@ -137,10 +132,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) tc::tmem_alloc(&tbase, L.tmem_cols);
   if (threadIdx.x == 0) {
-    tc::mbar_init(&full[0], L.nprodw);
-    tc::mbar_init(&full[1], L.nprodw);
-    tc::mbar_init(&empty[0], 1);
-    tc::mbar_init(&empty[1], 1);
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&sfull[s], 1);
+      tc::mbar_init(&sempty[s], g.ntask);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&ofull[b], L.nprodw);
+      tc::mbar_init(&oempty[b], 1);
+    }
     abort_flag = 0;
   }
   tc::fence_before();
@@ -151,19 +150,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nchunks = (M + kChunk - 1) / kChunk;
 
   if (warp == L.nprodw) {
+    // ---------------- copy warp: the columns' U1 / W blocks into the stage ring ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int c = 0; c < M; ++c) {
+        const int st = c % S;
+        if (c >= S && (abort_flag || !tc::mbar_wait(&sempty[st], ((c / S) - 1) & 1))) {
+          abort_flag = 1;
+          break;
+        }
+        const CacheDesc d = cdesc[(int64_t)c * q + k];
+        issue_item(stages + (size_t)st * SL.stride, SL, &sfull[st], &meta[st], cache, d, g, B1p, i1_0, i2_0, i3,
+                   nullptr, 0u);
+        issued = c + 1;
+      }
+      if (abort_flag)  // let the copies in flight land before the CTA exits
+        for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
+    }
+  } else if (warp == L.nprodw + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::instr_desc(128, P2, F::idfmt);
       const uint32_t sbo = L.KBA * 128;
       const int ksteps = L.KBA / 2;
-      for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
-        if (abort_flag || !tc::mbar_wait(&full[buf], (c >> 1) & 1)) {
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const int buf = ch & 1;
+        if (abort_flag || !tc::mbar_wait(&ofull[buf], (ch >> 1) & 1)) {
           abort_flag = 1;
           break;
         }
         tc::fence_after();
-        const bool fresh = (c % kFlush) == 0;
+        const bool fresh = (ch % kFlush) == 0;
 #pragma unroll 1
         for (int m = 0; m < L.nmt; ++m) {
 #pragma unroll
@@ -177,15 +194,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        tc::commit(&empty[buf]);
+        tc::commit(&oempty[buf]);
       }
     }
     __syncwarp();
   } else {
-    // ---------------- producers ----------------
+    // ---------------- producers: last mode product, operand split, fold, epilogue ----------------
     const int tid = threadIdx.x;
     const int ngroups = L.nprodw / 4;  // warpgroups that fold and drain the accumulators
     const int wq = warp & 3, wg = warp >> 2;
+    const bool task = warp < g.ntask;
+    int i1 = 0, u0 = 0;
+    bool ok = false;
+    if (task) g.task(i1_0, warp, lane, i1, u0, ok);
+    const int il = ok ? i1 - i1_0 : 0;
     bool s_valid = false;
     // D -> S (round-to-nearest FP32) by whole warpgroups; D must be complete
     auto fold = [&]() {
@@ -207,35 +229,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc::tmem_wait_st();
     };
-    WPrefetch pf;
-    pf.load(cache, cdesc, g, R, q, k, 0, min(kChunk, M), i2_0, i3, tid, nprod);
-    for (int c = 0; c < nchunks; ++c) {
-      const int buf = c & 1;
-      const int j0 = c * kChunk;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int buf = ch & 1;
+      const int j0 = ch * kChunk;
       const int jc = min(kChunk, M - j0);
-      const bool do_fold = c > 0 && (c % kFlush) == 0;
-      const ChunkSmem cs = fe.cs(buf);
-      float2* xs = fe.xs(buf);
-      for (int e = tid; e < kChunk * P; e += nprod) {
-        const int jj = e / P, i = e % P;
-        xs[e] = (jj < jc && s0 + i < p) ? X[(j0 + jj) + ldx * (s0 + i)] : make_float2(0.f, 0.f);
+      const bool do_fold = ch > 0 && (ch % kFlush) == 0;
+      // 1. the chunk's decompressed values for this warp's task: z[l][2 jj + e]
+      float z[kUQ][2 * kChunk];
+#pragma unroll
+      for (int jj = 0; jj < kChunk; ++jj) {
+        float2 zz[kUQ];
+#pragma unroll
+        for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
+        if (task && jj < jc) {
+          const int c = j0 + jj, st = c % S;
+          const bool ab = __any_sync(0xffffffffu, abort_flag != 0);
+          if (!ab && __all_sync(0xffffffffu, tc::mbar_wait(&sfull[st], (c / S) & 1))) {
+            const unsigned char* sb = stages + (size_t)st * SL.stride;
+            last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0, zz);
+          } else if (!ab && lane == 0) {
+            abort_flag = 1;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive1(&sempty[st]);
+        }
+#pragma unroll
+        for (int l = 0; l < kUQ; ++l) {
+          z[l][2 * jj] = zz[l].x;
+          z[l][2 * jj + 1] = zz[l].y;
+        }
       }
-      pf.store(cs, g, R, jc, tid, nprod);
-      bar_sync(1, nprod);
-      if (j0 + kChunk < M)
-        pf.load(cache, cdesc, g, R, q, k, j0 + kChunk, min(kChunk, M - j0 - kChunk), i2_0, i3, tid, nprod);
-      if (c >= 2 || do_fold) {
-        // operand buffer free once chunk c-2 is consumed; folding D needs chunk c-1 done
-        const int wc = do_fold ? c - 1 : c - 2;
-        if (!abort_flag && !tc::mbar_wait(&empty[wc & 1], (wc >> 1) & 1)) abort_flag = 1;
+      // 2. operand buffer free once chunk ch-2 is consumed; folding D needs chunk ch-1 done
+      if (ch >= 2 || do_fold) {
+        const int wc = do_fold ? ch - 1 : ch - 2;
+        bool bad = abort_flag != 0;
+        if (!bad) bad = !tc::mbar_wait(&oempty[wc & 1], (wc >> 1) & 1);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) abort_flag = 1;
         tc::fence_after();
-        if (do_fold && !abort_flag) {
+        if (do_fold && !__any_sync(0xffffffffu, abort_flag != 0)) {
           fold();
           s_valid = true;
         }
       }
-      if (!abort_flag) {
-        // B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk
+      if (!__any_sync(0xffffffffu, abort_flag != 0)) {
+        // 3. B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk, from X^T
         const int nk16 = 2 * kChunk / NF;
         for (int e = tid; e < P2 * nk16; e += nprod) {
           const int n = e / nk16, kc = e % nk16;
@@ -244,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < NF; ++i) {
             const int kk = kc * NF + i;
-            const float2 v = xs[(kk >> 1) * P + s];
-            const int ei = kk & 1;
+            const int jj = kk >> 1, ei = kk & 1;
+            const float2 v = jj < jc ? XT[(int64_t)(j0 + jj) * pst + s0 + s] : make_float2(0.f, 0.f);
             x[i] = eo == ei ? v.x : (eo == 0 ? -v.y : v.y);
           }
           uint32_t t[F::terms][4];
@@ -254,30 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int term = 0; term < F::terms; ++term)
             st_shared_v4(tc::smem_u32(b_op(buf, term)) + tc::core_off(n, kc, L.KBA), t[term]);
         }
-        // A operand: rows of this warp's task (u = u0 + l, lane -> i1); K = 2*kChunk reals
-        if (warp < g.ntask) {
-          int i1, u0;
-          bool ok;
-          g.task(i1_0, warp, lane, i1, u0, ok);
-          float z[kUQ][2 * kChunk];
-#pragma unroll
-          for (int jj = 0; jj < kChunk; ++jj) {
-            float2 zz[kUQ];
-            if (jj < jc) {
-              const CacheDesc d = cs.cd[jj];
-              const int t1 = i1_0 / g.B1, il = ok ? i1 - i1_0 : 0;
-              last_mode4(cache + d.uoff + (int64_t)t1 * d.r1p * B1p + il, B1p, d.r1, ok,
-                         cs.W + (size_t)jj * R * g.NUp, g.NUp, u0, zz);
-            } else {
-#pragma unroll
-              for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int l = 0; l < kUQ; ++l) {
-              z[l][2 * jj] = zz[l].x;
-              z[l][2 * jj + 1] = zz[l].y;
-            }
-          }
+        // 4. A operand: rows of this warp's task (u = u0 + l, lane -> i1); K = 2*kChunk reals
+        if (task) {
 #pragma unroll
           for (int l = 0; l < kUQ; ++l) {
             const int rho = Geo::row(warp, l, lane);
@@ -298,25 +313,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_proxy_async();
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full[buf]);
+      if (lane == 0) mbar_arrive1(&ofull[buf]);
     }
     // drain: the last commit covers every MMA
-    if (nchunks > 0 && !abort_flag &&
-        !tc::mbar_wait(&empty[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1))
-      abort_flag = 1;
+    {
+      bool bad = abort_flag != 0;
+      if (!bad && nchunks > 0) bad = !tc::mbar_wait(&oempty[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+      if (__any_sync(0xffffffffu, bad) && lane == 0) abort_flag = 1;
+    }
     tc::fence_after();
-    if (!abort_flag && wg < ngroups) {
+    if (!__any_sync(0xffffffffu, abort_flag != 0) && wg < ngroups) {
       const int64_t nv = (int64_t)g.n1 * g.n2 * g.n3;
       for (int m = wg; m < L.nmt; m += ngroups) {
         // row rho = 128 m + 32 wq + lane = (tk * kUQ + l) * 32 + lane
         const int rg = m * 4 + wq;
         const int tk = rg / kUQ, l = rg % kUQ;
-        int i1 = 0, u0 = 0;
-        bool ok = false;
-        if (tk < g.ntask) g.task(i1_0, tk, lane, i1, u0, ok);
-        const int u = u0 + l;
-        ok = ok && u < g.NU && (i2_0 + u) < g.n2;
-        const int64_t v = i1 + (int64_t)g.n1 * ((i2_0 + u) + (int64_t)g.n2 * i3);
+        int ei1 = 0, eu0 = 0;
+        bool eok = false;
+        if (tk < g.ntask) g.task(i1_0, tk, lane, ei1, eu0, eok);
+        const int u = eu0 + l;
+        eok = eok && u < g.NU && (i2_0 + u) < g.n2;
+        const int64_t v = ei1 + (int64_t)g.n1 * ((i2_0 + u) + (int64_t)g.n2 * i3);
         const uint32_t lanebase = (uint32_t)(wq * 32) << 16;
 #pragma unroll 1
         for (int c0 = 0; c0 < P2; c0 += 16) {
@@ -328,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) vals[i] += sv[i];
           }
-          if (ok) {
+          if (eok) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int s = s0 + c0 / 2 + i;
@@ -351,42 +368,51 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
   constexpr int P = P2 / 2;
   ZBC_TRY(build_decomp_cache(h, st));
   const int R = h.cache_r;
-  // rows limited by TMEM (D and S: 2 * nmt * P2 <= 512), by two shared-memory A buffers and by
-  // the block size (producer warps + the issuer <= 8); the largest tile that fits is taken.
+  const int B1p = tile_b1p(h.n1);
+  // rows limited by TMEM (D and S: 2 * nmt * P2 <= 512), by the block (<= 8 producer warps) and
+  // by shared memory (two operand buffers plus at least two stages); the largest tile that
+  // fits is taken, and the stages get the rest of shared memory
   const int tmem_rows = 128 * std::max(1, 256 / P2);
   const size_t budget = 220 * 1024;
   Geo g;
   TcLayout L;
+  StageLayout SL{};
+  int S = 0;
   size_t sm = 0;
-  int tasks = 7;
-  for (; tasks >= 1; --tasks) {
-    g = make_geo(h.n1, h.n2, h.n3, R, tasks, tmem_rows);
+  for (int tasks = kTcMaxTasks; tasks >= 1 && S == 0; --tasks) {
+    g = make_geo(h.n1, h.n2, h.n3, 0, tasks, tmem_rows);
+    if (g.ntask > kTcMaxTasks) continue;
     L.NR = g.ntask * kUQ * 32;
     L.nmt = L.NR / 128;
     L.KBA = 2 * kChunk * F::esz / 16;
     L.a_bytes = L.NR * L.KBA * 16;
     L.b_bytes = P2 * L.KBA * 16;
     L.nprodw = std::max(4, g.ntask);
-    sm = 2 * FrontEnd2::buf_bytes(R, g.NUp, kChunk * P) + 1024 +
-         (size_t)2 * F::terms * (L.a_bytes + L.b_bytes);
-    if (sm <= budget && g.ntask <= 7) break;
+    SL = StageLayout::make(R, B1p, g.NUp, 0, 0);
+    const size_t ops = 1024 + (size_t)2 * F::terms * (L.a_bytes + L.b_bytes);
+    if (ops + 2 * (size_t)SL.stride > budget) continue;
+    S = (int)std::min<size_t>(kMaxStages, (budget - ops) / SL.stride);
+    sm = (size_t)S * SL.stride + ops;
   }
   int cols = 32;
   while (cols < 2 * L.nmt * P2) cols <<= 1;
   L.tmem_cols = cols;
-  if (tasks < 1 || sm > budget || cols > 512) {
-    set_error("tensor-core layout does not fit (rank %d, smem %zu, tmem %d)", R, sm, cols);
+  if (S < 2 || cols > 512) {
+    set_error("tensor-core layout does not fit (rank %d, tmem %d)", R, cols);
     return ZBC_EINVAL;
   }
+  const float2* XT;
+  int pst;
+  ZBC_TRY(transpose_rhs(h, X, ldx, p, P, &XT, &pst, st));
   static bool attr_set = false;
   if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_tc_kernel<FMT, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 221 * 1024));
+    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_tc_kernel<FMT, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)budget));
     attr_set = true;
   }
-  int* err = (int*)h.work_err.ptr;
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
-  matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, R, L,
-                                                                   X, ldx, p, Y, ldy, err);
+  matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 2), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL,
+                                                                   S, L, XT, pst, p, Y, ldy, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;

@@ -23,6 +23,11 @@ namespace zbc {
 
 constexpr int kMaxStages = 8;
 
+// X^T (M rows of pst >= p complex64, zero padded to a whole number of `chunk`-wide RHS chunks,
+// pst even) in the handle's workspace, so that a column's RHS values are one aligned run
+int transpose_rhs(Handle& h, const float2* X, int64_t ldx, int p, int chunk, const float2** XT, int* pst,
+                  cudaStream_t st);
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
                : "memory");
@@ -58,21 +63,39 @@ struct StageLayout {
 
 // Last mode product of one column for kUQ voxels sharing i1, from the staged blocks:
 //   z[l] = sum_a U1s[a][il] Ws[u0 + l][a],  a < r1p (the pad entries are zero)
+// Even and odd a accumulate in separate chains (twice the independent FMAs in flight) and the
+// next a-pair's operands are loaded before the current pair's FMAs.
 __device__ __forceinline__ void last_mode_staged(const float2* U1s, int B1p, int il, const float2* Ws, int r1p,
                                                  int u0, float2 (&z)[kUQ]) {
+  float2 ze[kUQ], zo[kUQ];
 #pragma unroll
-  for (int l = 0; l < kUQ; ++l) z[l] = make_float2(0.f, 0.f);
+  for (int l = 0; l < kUQ; ++l) ze[l] = zo[l] = make_float2(0.f, 0.f);
   const float2* u = U1s + il;
-#pragma unroll 2
+  const float4* w4 = reinterpret_cast<const float4*>(Ws + u0 * r1p);
+  const int ws = r1p / 2;  // float4 stride between consecutive u
+  float2 x0 = u[0], x1 = u[B1p];
+  float4 w[kUQ];
+#pragma unroll
+  for (int l = 0; l < kUQ; ++l) w[l] = w4[l * ws];
   for (int a = 0; a < r1p; a += 2) {
-    const float2 x0 = u[a * B1p], x1 = u[(a + 1) * B1p];
+    const bool more = a + 2 < r1p;
+    const int an = more ? a + 2 : a;
+    const float2 nx0 = u[an * B1p], nx1 = u[(an + 1) * B1p];
+    float4 nw[kUQ];
+#pragma unroll
+    for (int l = 0; l < kUQ; ++l) nw[l] = w4[l * ws + an / 2];
 #pragma unroll
     for (int l = 0; l < kUQ; ++l) {
-      const float4 w = *reinterpret_cast<const float4*>(Ws + (u0 + l) * r1p + a);
-      z[l] = cfma(x0, make_float2(w.x, w.y), z[l]);
-      z[l] = cfma(x1, make_float2(w.z, w.w), z[l]);
+      ze[l] = cfma(x0, make_float2(w[l].x, w[l].y), ze[l]);
+      zo[l] = cfma(x1, make_float2(w[l].z, w[l].w), zo[l]);
     }
+    x0 = nx0;
+    x1 = nx1;
+#pragma unroll
+    for (int l = 0; l < kUQ; ++l) w[l] = nw[l];
   }
+#pragma unroll
+  for (int l = 0; l < kUQ; ++l) z[l] = make_float2(ze[l].x + zo[l].x, ze[l].y + zo[l].y);
 }
 
 // Producer side: issue the copies of item (column j, tile origin i1_0, i2_0, i3) into stage st.

@@ -91,6 +91,7 @@ struct Handle {
   TcPack* tc = nullptr;
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
+  int simt_warps = 0;              // compute warps per CTA of the FP32 products (0: default)
   ~Handle();
   int64_t nv() const { return (int64_t)n1 * n2 * n3; }
   int upload();          // copy desc to device (pool already on device)
