@@ -19,9 +19,10 @@
 // region S; Y = S + D at the end.
 //
 // Warp roles: a copy warp streams each column's U1 / W blocks into the stage ring of stage.cuh
-// (cp.async.bulk); the front-end ("producer") warps each own one task of the tile, form its
-// last mode product from the staged blocks and fill the operands of a chunk; one more warp
-// issues the MMAs.  Two operand buffers alternate; an mbarrier "full" per buffer (one arrival
+// (cp.async.bulk); the front-end ("producer") warps form the last mode product of one task of
+// the tile from the staged blocks and fill the operands of a chunk -- two warps per task, one
+// for each half of the chunk's columns, so that more warps hide the shared-memory latency;
+// one more warp issues the MMAs.  Two operand buffers alternate; an mbarrier "full" per buffer (one arrival
 // per producer warp) hands a filled buffer to the issuer, and tcgen05.commit on an mbarrier
 // "empty" per buffer hands it back once the tensor cores have consumed it.  No CTA-wide barrier
 // is taken between the prologue and the epilogue.
@@ -34,8 +35,8 @@
 namespace zbc {
 
 constexpr int kFlush = 4;       // chunks accumulated in D before it is folded into S
-constexpr int kTcMaxTasks = 8;  // producer warps with a task, at most
-constexpr int kTcThreads = 32 * (kTcMaxTasks + 2);  // + the copy warp and the MMA issuer
+constexpr int kTcMaxTasks = 6;  // tasks per tile, at most (two producer warps each)
+constexpr int kTcThreads = 32 * (2 * kTcMaxTasks + 2);  // + the copy warp and the MMA issuer
 
 struct TcPack {
   int dummy;
@@ -87,6 +88,10 @@ __device__ __forceinline__ void split_words(const float (&x)[NF], uint32_t (&t)[
       }
     }
   }
+}
+
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t w0, uint32_t w1) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(w0), "r"(w1) : "memory");
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t (&w)[4]) {
@@ -151,22 +156,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == L.nprodw) {
     // ---------------- copy warp: the columns' U1 / W blocks into the stage ring ----------------
-    if (lane == 0) {
-      int issued = 0;
-      for (int c = 0; c < M; ++c) {
-        const int st = c % S;
-        if (c >= S && (abort_flag || !tc::mbar_wait(&sempty[st], ((c / S) - 1) & 1))) {
-          abort_flag = 1;
+    // lane l holds the cache entry of column c0 + l of the current batch of 32 columns
+    int issued = 0;
+    for (int c0 = 0; c0 < M && !__any_sync(0xffffffffu, abort_flag != 0); c0 += 32) {
+      CacheDesc mine{};
+      if (c0 + lane < M) mine = cdesc[(int64_t)(c0 + lane) * q + k];
+      const int nb = min(32, M - c0);
+      for (int i = 0; i < nb; ++i) {
+        CacheDesc d;
+        d.woff = __shfl_sync(0xffffffffu, mine.woff, i);
+        d.uoff = __shfl_sync(0xffffffffu, mine.uoff, i);
+        d.r1 = __shfl_sync(0xffffffffu, mine.r1, i);
+        d.r1p = __shfl_sync(0xffffffffu, mine.r1p, i);
+        const int c = c0 + i, st = c % S;
+        bool bad = false;
+        if (lane == 0 && c >= S) bad = abort_flag || !tc::mbar_wait(&sempty[st], ((c / S) - 1) & 1);
+        if (__shfl_sync(0xffffffffu, bad, 0)) {
+          if (lane == 0) abort_flag = 1;
           break;
         }
-        const CacheDesc d = cdesc[(int64_t)c * q + k];
-        issue_item(stages + (size_t)st * SL.stride, SL, &sfull[st], &meta[st], cache, d, g, B1p, i1_0, i2_0, i3,
-                   nullptr, 0u);
+        if (lane == 0)
+          issue_item(stages + (size_t)st * SL.stride, SL, &sfull[st], &meta[st], cache, d, g, B1p, i1_0, i2_0, i3,
+                     nullptr, 0u);
         issued = c + 1;
       }
-      if (abort_flag)  // let the copies in flight land before the CTA exits
-        for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
     }
+    if (lane == 0 && abort_flag)  // let the copies in flight land before the CTA exits
+      for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
   } else if (warp == L.nprodw + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -203,10 +219,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int tid = threadIdx.x;
     const int ngroups = L.nprodw / 4;  // warpgroups that fold and drain the accumulators
     const int wq = warp & 3, wg = warp >> 2;
-    const bool task = warp < g.ntask;
+    // warps tk and tk + ntask share task tk, each taking half of the chunk's columns
+    const bool task = warp < 2 * g.ntask;
+    const int tk = warp % g.ntask, half = warp / g.ntask;
     int i1 = 0, u0 = 0;
     bool ok = false;
-    if (task) g.task(i1_0, warp, lane, i1, u0, ok);
+    if (task) g.task(i1_0, tk, lane, i1, u0, ok);
     const int il = ok ? i1 - i1_0 : 0;
     bool s_valid = false;
     // D -> S (round-to-nearest FP32) by whole warpgroups; D must be complete
@@ -234,32 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int j0 = ch * kChunk;
       const int jc = min(kChunk, M - j0);
       const bool do_fold = ch > 0 && (ch % kFlush) == 0;
-      // 1. the chunk's decompressed values for this warp's task: z[l][2 jj + e]
-      float z[kUQ][2 * kChunk];
-#pragma unroll
-      for (int jj = 0; jj < kChunk; ++jj) {
-        float2 zz[kUQ];
-#pragma unroll
-        for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
-        if (task && jj < jc) {
-          const int c = j0 + jj, st = c % S;
-          const bool ab = __any_sync(0xffffffffu, abort_flag != 0);
-          if (!ab && __all_sync(0xffffffffu, tc::mbar_wait(&sfull[st], (c / S) & 1))) {
-            const unsigned char* sb = stages + (size_t)st * SL.stride;
-            last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0, zz);
-          } else if (!ab && lane == 0) {
-            abort_flag = 1;
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive1(&sempty[st]);
-        }
-#pragma unroll
-        for (int l = 0; l < kUQ; ++l) {
-          z[l][2 * jj] = zz[l].x;
-          z[l][2 * jj + 1] = zz[l].y;
-        }
-      }
-      // 2. operand buffer free once chunk ch-2 is consumed; folding D needs chunk ch-1 done
+      // 1. operand buffer free once chunk ch-2 is consumed; folding D needs chunk ch-1 done
       if (ch >= 2 || do_fold) {
         const int wc = do_fold ? ch - 1 : ch - 2;
         bool bad = abort_flag != 0;
@@ -271,42 +264,91 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           s_valid = true;
         }
       }
-      if (!__any_sync(0xffffffffu, abort_flag != 0)) {
-        // 3. B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk, from X^T
-        const int nk16 = 2 * kChunk / NF;
-        for (int e = tid; e < P2 * nk16; e += nprod) {
-          const int n = e / nk16, kc = e % nk16;
-          const int s = n >> 1, eo = n & 1;
-          float x[NF];
+      // 2. this thread's share of the chunk's X values (loaded now, used after the last mode)
+      constexpr int nk16 = 2 * kChunk / NF;
+      constexpr int kBMax = (P2 * nk16 + 127) / 128;  // B elements per thread (>= 128 producers)
+      float2 xv[kBMax][NF / 2];
 #pragma unroll
-          for (int i = 0; i < NF; ++i) {
-            const int kk = kc * NF + i;
-            const int jj = kk >> 1, ei = kk & 1;
-            const float2 v = jj < jc ? XT[(int64_t)(j0 + jj) * pst + s0 + s] : make_float2(0.f, 0.f);
-            x[i] = eo == ei ? v.x : (eo == 0 ? -v.y : v.y);
-          }
-          uint32_t t[F::terms][4];
-          split_words<FMT, NF>(x, t);
+      for (int b = 0; b < kBMax; ++b) {
+        const int e = tid + b * nprod;
+        const int n = e / nk16, kc = e % nk16;
 #pragma unroll
-          for (int term = 0; term < F::terms; ++term)
-            st_shared_v4(tc::smem_u32(b_op(buf, term)) + tc::core_off(n, kc, L.KBA), t[term]);
+        for (int i = 0; i < NF / 2; ++i) {
+          const int jj = kc * (NF / 2) + i;
+          xv[b][i] = (e < P2 * nk16 && jj < jc) ? XT[(int64_t)(j0 + jj) * pst + s0 + (n >> 1)] : make_float2(0.f, 0.f);
         }
-        // 4. A operand: rows of this warp's task (u = u0 + l, lane -> i1); K = 2*kChunk reals
-        if (task) {
+      }
+      // 3. A operand: the last mode product of this warp's task for its columns of the chunk,
+      //    pairs {4g + 2 half, 4g + 2 half + 1} (so both halves consume the stage ring in order)
+      if (task) {
+#pragma unroll 1
+        for (int g4 = 0; g4 < kChunk / 4; ++g4) {
+          const int jj0 = 4 * g4 + 2 * half;
+          float x[kUQ][4];
 #pragma unroll
-          for (int l = 0; l < kUQ; ++l) {
-            const int rho = Geo::row(warp, l, lane);
+          for (int t = 0; t < 2; ++t) {
+            const int jj = jj0 + t;
+            float2 zz[kUQ];
 #pragma unroll
-            for (int kc = 0; kc < 2 * kChunk / NF; ++kc) {
-              float x[NF];
-#pragma unroll
-              for (int i = 0; i < NF; ++i) x[i] = z[l][kc * NF + i];
-              uint32_t t[F::terms][4];
-              split_words<FMT, NF>(x, t);
-#pragma unroll
-              for (int term = 0; term < F::terms; ++term)
-                st_shared_v4(tc::smem_u32(a_op(buf, term)) + tc::core_off(rho, kc, L.KBA), t[term]);
+            for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
+            if (jj < jc) {
+              const int c = j0 + jj, st = c % S;
+              const bool ab = __any_sync(0xffffffffu, abort_flag != 0);
+              if (!ab && __all_sync(0xffffffffu, tc::mbar_wait(&sfull[st], (c / S) & 1))) {
+                const unsigned char* sb = stages + (size_t)st * SL.stride;
+                last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0,
+                                 zz);
+              } else if (!ab && lane == 0) {
+                abort_flag = 1;
+              }
+              __syncwarp();
+              if (lane == 0) mbar_arrive1(&sempty[st]);
             }
+#pragma unroll
+            for (int l = 0; l < kUQ; ++l) {
+              x[l][2 * t] = zz[l].x;
+              x[l][2 * t + 1] = zz[l].y;
+            }
+          }
+          if (!__any_sync(0xffffffffu, abort_flag != 0)) {
+            // reals 2 jj0 .. 2 jj0 + 3 of each row: 8 bytes (bf16) or 16 bytes (tf32) at
+            const uint32_t kb = 2u * jj0 * F::esz;  // byte offset along K
+#pragma unroll
+            for (int l = 0; l < kUQ; ++l) {
+              uint32_t t[F::terms][4];
+              split_words<FMT, 4>(x[l], t);
+              const int rho = Geo::row(tk, l, lane);
+#pragma unroll
+              for (int term = 0; term < F::terms; ++term) {
+                const uint32_t addr = tc::smem_u32(a_op(buf, term)) + tc::core_off(rho, kb / 16, L.KBA) + kb % 16;
+                if constexpr (F::esz == 2)
+                  st_shared_v2(addr, t[term][0], t[term][1]);
+                else
+                  st_shared_v4(addr, t[term]);
+              }
+            }
+          }
+        }
+      }
+      // 4. B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk
+      if (!__any_sync(0xffffffffu, abort_flag != 0)) {
+#pragma unroll
+        for (int b = 0; b < kBMax; ++b) {
+          const int e = tid + b * nprod;
+          if (e < P2 * nk16) {
+            const int n = e / nk16, kc = e % nk16;
+            const int eo = n & 1;
+            float x[NF];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+              const float2 v = xv[b][i >> 1];
+              x[i] = eo == (i & 1) ? v.x : (eo == 0 ? -v.y : v.y);
+            }
+            uint32_t t[F::terms][4];
+            split_words<FMT, NF>(x, t);
+#pragma unroll
+            for (int term = 0; term < F::terms; ++term)
+              st_shared_v4(tc::smem_u32(b_op(buf, term)) + tc::core_off(n, kc, L.KBA), t[term]);
           }
         }
       }
@@ -387,7 +429,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
     L.KBA = 2 * kChunk * F::esz / 16;
     L.a_bytes = L.NR * L.KBA * 16;
     L.b_bytes = P2 * L.KBA * 16;
-    L.nprodw = std::max(4, g.ntask);
+    L.nprodw = std::max(4, 2 * g.ntask);
     SL = StageLayout::make(R, B1p, g.NUp, 0, 0);
     const size_t ops = 1024 + (size_t)2 * F::terms * (L.a_bytes + L.b_bytes);
     if (ops + 2 * (size_t)SL.stride > budget) continue;
