@@ -123,10 +123,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ volatile int abort_flag;
   unsigned char* stages = smem;
   unsigned char* ops = (unsigned char*)(((uintptr_t)(smem + (size_t)S * SL.stride) + 1023) & ~(uintptr_t)1023);
-  auto a_op = [&](int buf, int term) { return ops + (size_t)(buf * F::terms + term) * L.a_bytes; };
-  auto b_op = [&](int buf, int term) {
-    return ops + (size_t)2 * F::terms * L.a_bytes + (size_t)(buf * F::terms + term) * L.b_bytes;
-  };
+  // one operand buffer: a chunk's operands are written once the previous chunk's MMAs are done
+  // (the wait comes after the first columns' last mode products, so it rarely blocks), which
+  // leaves shared memory for a deeper stage ring
+  auto a_op = [&](int, int term) { return ops + (size_t)term * L.a_bytes; };
+  auto b_op = [&](int, int term) { return ops + (size_t)F::terms * L.a_bytes + (size_t)term * L.b_bytes; };
   const int k = blockIdx.y;
   const int s0 = blockIdx.z * (P2 / 2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -252,18 +253,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int j0 = ch * kChunk;
       const int jc = min(kChunk, M - j0);
       const bool do_fold = ch > 0 && (ch % kFlush) == 0;
-      // 1. operand buffer free once chunk ch-2 is consumed; folding D needs chunk ch-1 done
-      if (ch >= 2 || do_fold) {
-        const int wc = do_fold ? ch - 1 : ch - 2;
+      // 1. before the first store: the operand buffer is free, and D complete for a fold, once
+      //    chunk ch-1's MMAs are done
+      bool freed = ch == 0;
+      auto ensure_free = [&]() {
+        if (freed) return;
+        freed = true;
         bool bad = abort_flag != 0;
-        if (!bad) bad = !tc::mbar_wait(&oempty[wc & 1], (wc >> 1) & 1);
+        if (!bad) bad = !tc::mbar_wait(&oempty[(ch - 1) & 1], ((ch - 1) >> 1) & 1);
         if (__any_sync(0xffffffffu, bad) && lane == 0) abort_flag = 1;
         tc::fence_after();
         if (do_fold && !__any_sync(0xffffffffu, abort_flag != 0)) {
           fold();
           s_valid = true;
         }
-      }
+      };
       // 2. this thread's share of the chunk's X values (loaded now, used after the last mode)
       constexpr int nk16 = 2 * kChunk / NF;
       constexpr int kBMax = (P2 * nk16 + 127) / 128;  // B elements per thread (>= 128 producers)
@@ -310,6 +314,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               x[l][2 * t + 1] = zz[l].y;
             }
           }
+          ensure_free();
           if (!__any_sync(0xffffffffu, abort_flag != 0)) {
             // reals 2 jj0 .. 2 jj0 + 3 of each row: 8 bytes (bf16) or 16 bytes (tf32) at
             const uint32_t kb = 2u * jj0 * F::esz;  // byte offset along K
@@ -331,6 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       // 4. B operand: rows n = 2s + e_out (P2 rows), K = 2*kChunk reals of this chunk
+      ensure_free();
       if (!__any_sync(0xffffffffu, abort_flag != 0)) {
 #pragma unroll
         for (int b = 0; b < kBMax; ++b) {
@@ -431,7 +437,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
     L.b_bytes = P2 * L.KBA * 16;
     L.nprodw = std::max(4, 2 * g.ntask);
     SL = StageLayout::make(R, B1p, g.NUp, 0, 0);
-    const size_t ops = 1024 + (size_t)2 * F::terms * (L.a_bytes + L.b_bytes);
+    const size_t ops = 1024 + (size_t)F::terms * (L.a_bytes + L.b_bytes);
     if (ops + 2 * (size_t)SL.stride > budget) continue;
     S = (int)std::min<size_t>(kMaxStages, (budget - ops) / SL.stride);
     sm = (size_t)S * SL.stride + ops;
