@@ -56,8 +56,12 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  * FP32_SIMT : complex FP32 on CUDA cores (the plain form).
  * TF32X3    : tensor cores, tcgen05 kind::tf32, each operand split hi+lo, 3 products, FP32 accumulation.
  * BF16X3    : tensor cores, tcgen05 kind::f16 with bf16 operands split into 3 terms
- *             (hi+mid+lo), the 6 products above 2^-24, FP32 accumulation. */
-typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2 } zbc_precision;
+ *             (hi+mid+lo), the 6 products above 2^-24, FP32 accumulation.
+ * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
+ *             right-hand-side class; before any tuning, BF16X3 for the forward product when
+ *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,
+ *             but their last bits differ, so AUTO results depend on the tuning. */
+typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2, ZBC_AUTO = 3 } zbc_precision;
 
 typedef enum { ZBC_HOSVD = 0, ZBC_RANDOMIZED_LEARNED = 1, ZBC_RANDOMIZED_FIXED = 2 } zbc_tucker_method;
 
@@ -241,6 +245,7 @@ int zbc_matvec(const zbc_handle* h, const void* X, int64_t ldx, int p, void* Y, 
  *   Phi : device complex64, (q*n_v) x p, ldphi >= q*n_v
  *   Psi : device complex64, m x p, ldpsi >= m; overwritten
  * Partial sums over voxel tiles are reduced in a fixed order (deterministic).
+ * prec: ZBC_FP32_SIMT or ZBC_AUTO; the adjoint has no tensor-core form (ZBC_EINVAL).
  */
 int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi,
                 int64_t ldpsi, zbc_precision prec, zbc_stream stream);
@@ -264,6 +269,19 @@ int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void
  */
 int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi, int64_t ldpsi,
                         zbc_stream stream);
+
+/*
+ * zbc_tune -- autotuner of the product kernels (no counterpart in the paper).  Times, on this
+ * handle with p right-hand sides (zero-filled scratch operands), every variant of
+ *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3
+ *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA
+ * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
+ * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the adjoint's choice).
+ *   times_ms_host : optional float[6], the variants' times in the order above (ms per call;
+ *                   +inf for a variant that does not fit this handle)
+ * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
+ */
+int zbc_tune(zbc_handle* h, int p, zbc_stream stream, float* times_ms_host);
 
 /*
  * zbc_product_status -- device-side status of this handle's product kernels (zbc_matvec,

@@ -32,8 +32,6 @@ int assemble_columns_c128(const GreenGeom& G, const int32_t* cols, int ncols, do
 int hosvd_compress(const void* cols, int64_t ld, int ncols, int n1, int n2, int n3, int q, zbc_dtype dt, double tol,
                    std::vector<int32_t>& ranks, float2** pool, int64_t* elems, double* max_err, int batch_cols,
                    cudaStream_t st);
-int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
-int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st);
 
 __global__ void aca_row_kernel(GreenGeom G, int64_t v, int k, double2* __restrict__ out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,7 +344,7 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
         std::vector<float2> c32(K);
         for (int l = 0; l < K; ++l) c32[l] = make_float2((float)c[l].x, (float)c[l].y);
         ZBC_TRY_CUDA(cudaMemcpyAsync(d_c.p, c32.data(), sizeof(float2) * K, cudaMemcpyHostToDevice, st));
-        ZBC_TRY(matvec_simt(hh->h, (const float2*)d_c.p, K, 1, (float2*)d_tmp32.p, N, st));
+        ZBC_TRY(matvec_simt(hh->h, (const float2*)d_c.p, K, 1, (float2*)d_tmp32.p, N, 9, st));
         aca_sub_c64_kernel<<<ceil_div(N, 256), 256, 0, st>>>((double2*)d_col.p, (const float2*)d_tmp32.p, N);
         count_launch();
       }
@@ -374,7 +372,7 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
       } else {
         aca_to_c64_kernel<<<ceil_div(N, 256), 256, 0, st>>>((const double2*)d_col.p, (float2*)d_col32.p, N);
         count_launch();
-        ZBC_TRY(rmatvec_simt(hh->h, (const float2*)d_col32.p, N, 1, (float2*)d_tmp32.p, K, st));
+        ZBC_TRY(rmatvec_simt(hh->h, (const float2*)d_col32.p, N, 1, (float2*)d_tmp32.p, K, 9, st));
         std::vector<float2> w(K);
         ZBC_TRY_CUDA(cudaMemcpyAsync(w.data(), d_tmp32.p, sizeof(float2) * K, cudaMemcpyDeviceToHost, st));
         ZBC_TRY_CUDA(cudaStreamSynchronize(st));

@@ -1,16 +1,43 @@
-// zbc_matvec / zbc_rmatvec: argument checks, the ACA pre/post products (Sec. III.B) and
-// dispatch to the arithmetic form (FP32 SIMT or a tensor-core form).
+// zbc_matvec / zbc_rmatvec: argument checks, the ACA pre/post products (Sec. III.B), dispatch to
+// the arithmetic form (FP32 SIMT or a tensor-core form), the autotuner and the product status.
+#include <cmath>
+
 #include "zbc_internal.cuh"
 
 namespace zbc {
-int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
-int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st);
 int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, zbc_precision prec,
               cudaStream_t st);
-int rmatvec_tc(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, zbc_precision prec,
-               cudaStream_t st);
 int aca_pre(const Handle& h, const float2* X, int64_t ldx, int p, float2* Xp, cudaStream_t st);
 int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ldpsi, cudaStream_t st);
+
+// Y = Z X with an explicit form (prec != AUTO) and SIMT CTA shape
+static int matvec_impl(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, zbc_precision prec,
+                       int warps, cudaStream_t st) {
+  const float2* Xe = X;
+  int64_t ldxe = ldx;
+  if (h.has_v) {
+    ZBC_TRY(h.work_x.ensure(sizeof(float2) * (size_t)h.M * p));
+    ZBC_TRY(aca_pre(h, X, ldx, p, (float2*)h.work_x.ptr, st));
+    Xe = (const float2*)h.work_x.ptr;
+    ldxe = h.M;
+  }
+  if (prec == ZBC_FP32_SIMT) return matvec_simt(h, Xe, ldxe, p, Y, ldy, warps, st);
+  return matvec_tc(h, Xe, ldxe, p, Y, ldy, prec, st);
+}
+
+static int rmatvec_impl(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* Psi, int64_t ldpsi, int warps,
+                        cudaStream_t st) {
+  float2* out = Psi;
+  int64_t ldo = ldpsi;
+  if (h.has_v) {
+    ZBC_TRY(h.work_x.ensure(sizeof(float2) * (size_t)h.M * p));
+    out = (float2*)h.work_x.ptr;
+    ldo = h.M;
+  }
+  ZBC_TRY(rmatvec_simt(h, Phi, ldphi, p, out, ldo, warps, st));
+  if (h.has_v) return aca_post(h, out, p, Psi, ldpsi, st);
+  return ZBC_OK;
+}
 }  // namespace zbc
 
 using namespace zbc;
@@ -23,17 +50,13 @@ extern "C" int zbc_matvec(const zbc_handle* hh, const void* X, int64_t ldx, int 
   ZBC_CHECK_ARG(p >= 1 && p <= 1024, "p must be in [1, 1024] (got %d)", p);
   ZBC_CHECK_ARG(ldx >= h.m, "ldx (%lld) < m (%d)", (long long)ldx, h.m);
   ZBC_CHECK_ARG(ldy >= (int64_t)h.q * h.nv(), "ldy < q*n_v");
-  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3, "unknown precision %d", (int)prec);
-  const float2* Xe = (const float2*)X;
-  int64_t ldxe = ldx;
-  if (h.has_v) {
-    ZBC_TRY(h.work_x.ensure(sizeof(float2) * (size_t)h.M * p));
-    ZBC_TRY(aca_pre(h, (const float2*)X, ldx, p, (float2*)h.work_x.ptr, stream));
-    Xe = (const float2*)h.work_x.ptr;
-    ldxe = h.M;
-  }
-  if (prec == ZBC_FP32_SIMT) return matvec_simt(h, Xe, ldxe, p, (float2*)Y, ldy, stream);
-  return matvec_tc(h, Xe, ldxe, p, (float2*)Y, ldy, prec, stream);
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO,
+                "unknown precision %d", (int)prec);
+  const int cls = rhs_class(p);
+  int warps = h.tune_fwd_warps[cls];
+  if (prec == ZBC_AUTO)
+    prec = h.tune_fwd_prec[cls] >= 0 ? (zbc_precision)h.tune_fwd_prec[cls] : (p >= 8 ? ZBC_BF16X3 : ZBC_FP32_SIMT);
+  return matvec_impl(h, (const float2*)X, ldx, p, (float2*)Y, ldy, prec, warps, (cudaStream_t)stream);
 }
 
 extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi, int p, void* Psi, int64_t ldpsi,
@@ -44,18 +67,80 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   ZBC_CHECK_ARG(p >= 1 && p <= 1024, "p must be in [1, 1024] (got %d)", p);
   ZBC_CHECK_ARG(ldphi >= (int64_t)h.q * h.nv(), "ldphi < q*n_v");
   ZBC_CHECK_ARG(ldpsi >= h.m, "ldpsi (%lld) < m (%d)", (long long)ldpsi, h.m);
-  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3, "unknown precision %d", (int)prec);
-  float2* out = (float2*)Psi;
-  int64_t ldo = ldpsi;
-  if (h.has_v) {
-    ZBC_TRY(h.work_x.ensure(sizeof(float2) * (size_t)h.M * p));
-    out = (float2*)h.work_x.ptr;
-    ldo = h.M;
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO,
+                "unknown precision %d", (int)prec);
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_AUTO,
+                "the adjoint product has no tensor-core form: use ZBC_FP32_SIMT or ZBC_AUTO");
+  return rmatvec_impl(h, (const float2*)Phi, ldphi, p, (float2*)Psi, ldpsi, h.tune_adj_warps[rhs_class(p)],
+                      (cudaStream_t)stream);
+}
+
+extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_ms_host) {
+  clear_error();
+  ZBC_CHECK_ARG(hh, "zbc_tune: null handle");
+  ZBC_CHECK_ARG(p >= 1 && p <= 1024, "p must be in [1, 1024] (got %d)", p);
+  Handle& h = hh->h;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t rows = (int64_t)h.q * h.nv();
+  DevBuf X, Y, Phi, Psi;
+  ZBC_TRY(X.ensure(sizeof(float2) * (size_t)h.m * p));
+  ZBC_TRY(Psi.ensure(sizeof(float2) * (size_t)h.m * p));
+  ZBC_TRY(Y.ensure(sizeof(float2) * (size_t)rows * p));
+  ZBC_TRY(Phi.ensure(sizeof(float2) * (size_t)rows * p));
+  ZBC_TRY_CUDA(cudaMemsetAsync(X.ptr, 0, X.bytes, st));
+  ZBC_TRY_CUDA(cudaMemsetAsync(Phi.ptr, 0, Phi.bytes, st));
+  cudaEvent_t e0, e1;
+  ZBC_TRY_CUDA(cudaEventCreate(&e0));
+  ZBC_TRY_CUDA(cudaEventCreate(&e1));
+  struct Variant {
+    bool fwd;
+    zbc_precision prec;
+    int warps;
+  };
+  const Variant vars[6] = {{true, ZBC_FP32_SIMT, 6}, {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
+                           {true, ZBC_BF16X3, 0},    {false, ZBC_FP32_SIMT, 6}, {false, ZBC_FP32_SIMT, 9}};
+  float t[6];
+  int status = ZBC_OK;
+  for (int i = 0; i < 6 && status == ZBC_OK; ++i) {
+    const Variant& v = vars[i];
+    auto run = [&]() {
+      return v.fwd ? matvec_impl(h, (const float2*)X.ptr, h.m, p, (float2*)Y.ptr, rows, v.prec, v.warps, st)
+                   : rmatvec_impl(h, (const float2*)Phi.ptr, rows, p, (float2*)Psi.ptr, h.m, v.warps, st);
+    };
+    t[i] = INFINITY;
+    if (run() != ZBC_OK) {  // a form that does not fit this handle is skipped
+      clear_error();
+      continue;
+    }
+    cudaError_t e = cudaEventRecord(e0, st);
+    int s = ZBC_OK;
+    for (int r = 0; r < 2 && s == ZBC_OK; ++r) s = run();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      set_error("zbc_tune: timing failed: %s", cudaGetErrorString(e));
+      status = ZBC_ECUDA;
+    } else if (s != ZBC_OK) {
+      status = s;
+    } else {
+      t[i] = ms / 2.f;
+    }
   }
-  int s = prec == ZBC_FP32_SIMT ? rmatvec_simt(h, (const float2*)Phi, ldphi, p, out, ldo, stream)
-                                : rmatvec_tc(h, (const float2*)Phi, ldphi, p, out, ldo, prec, stream);
-  if (s != ZBC_OK) return s;
-  if (h.has_v) return aca_post(h, out, p, (float2*)Psi, ldpsi, stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != ZBC_OK) return status;
+  const int cls = rhs_class(p);
+  int bf = 0, ba = 4;
+  for (int i = 1; i < 4; ++i)
+    if (t[i] < t[bf]) bf = i;
+  if (t[5] < t[4]) ba = 5;
+  h.tune_fwd_prec[cls] = (int8_t)vars[bf].prec;
+  h.tune_fwd_warps[cls] = (int8_t)vars[bf].warps;
+  h.tune_adj_warps[cls] = (int8_t)vars[ba].warps;
+  if (times_ms_host)
+    for (int i = 0; i < 6; ++i) times_ms_host[i] = t[i];
   return ZBC_OK;
 }
 

@@ -8,14 +8,13 @@
 // the bulk-copy stage pipeline of stage.cuh: warps 0 .. ntask-1 compute (one task of 32 i1 x
 // kUQ i2 each), warp ntask copies (and, in Algorithm 2, sums the warps' per-column results).
 #include <algorithm>
-#include <cstdlib>
 
 #include "stage.cuh"
 
 namespace zbc {
 
-// NT = compute warps per CTA at most (template): 6 (8 warps with the copy warp, up to 255
-// registers per thread) or 9 (10 warps, 168 registers); see simt_warps()
+// NT = compute warps per CTA at most (template): 6 (7 warps with the copy warp, up to 255
+// registers per thread) or 9 (10 warps, 168 registers); chosen per call (zbc_tune), default 9
 constexpr size_t kSmemBudget = 220 * 1024;
 
 // ---------------------------------------------------------------------------------------------
@@ -471,17 +470,6 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);
 }
 
-// compute warps per CTA: the handle's tuned choice if any, else ZBC_SIMT_WARPS (6 or 9) from the
-// environment, else 9
-static int simt_warps(const Handle& h) {
-  if (h.simt_warps == 6 || h.simt_warps == 9) return h.simt_warps;
-  static int env = [] {
-    const char* e = getenv("ZBC_SIMT_WARPS");
-    return e ? atoi(e) : 0;
-  }();
-  return env == 6 ? 6 : 9;
-}
-
 template <int NT>
 static int rmatvec_dispatch(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
                             float2* scratch, size_t scratch_bytes, cudaStream_t st) {
@@ -507,17 +495,20 @@ int rmatvec_simt_scratch(Handle& h, const float2* Phi, int64_t ldphi, int p, flo
     set_error("the handle's decompression cache is not built: call zbc_matvec or zbc_rmatvec on it once first");
     return ZBC_EINVAL;
   }
-  if (simt_warps(h) == 6) return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
+  if (h.tune_adj_warps[rhs_class(p)] == 6)
+    return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
   return rmatvec_dispatch<9>(h, Phi, ldphi, p, out, ldo, scratch, scratch_bytes, st);
 }
 
-int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
-  if (simt_warps(h) == 6) return matvec_dispatch<6>(h, X, ldx, p, Y, ldy, st);
+// warps: compute warps per CTA, 6 or 9 (anything else: 9)
+int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, int warps, cudaStream_t st) {
+  if (warps == 6) return matvec_dispatch<6>(h, X, ldx, p, Y, ldy, st);
   return matvec_dispatch<9>(h, X, ldx, p, Y, ldy, st);
 }
 
-int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st) {
-  if (simt_warps(h) == 6) return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
+int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, int warps,
+                 cudaStream_t st) {
+  if (warps == 6) return rmatvec_dispatch<6>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
   return rmatvec_dispatch<9>(h, Phi, ldphi, p, out, ldo, nullptr, 0, st);
 }
 

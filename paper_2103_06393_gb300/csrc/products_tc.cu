@@ -480,10 +480,5 @@ int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t
   return matvec_tc_fmt<ZBC_BF16X3>(h, X, ldx, p, Y, ldy, st);
 }
 
-int rmatvec_tc(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, zbc_precision prec,
-               cudaStream_t st) {
-  set_error("tensor-core adjoint not built yet");
-  return ZBC_EINVAL;
-}
 
 }  // namespace zbc

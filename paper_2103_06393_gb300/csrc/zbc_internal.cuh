@@ -91,7 +91,11 @@ struct Handle {
   TcPack* tc = nullptr;
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
-  int simt_warps = 0;              // compute warps per CTA of the FP32 products (0: default)
+  // autotuned choices per right-hand-side class (zbc_tune; -1 / 0 = untuned)
+  static constexpr int kPClasses = 8;
+  int8_t tune_fwd_prec[kPClasses] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int8_t tune_fwd_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int8_t tune_adj_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
   ~Handle();
   int64_t nv() const { return (int64_t)n1 * n2 * n3; }
   int upload();          // copy desc to device (pool already on device)
@@ -124,7 +128,20 @@ __host__ __device__ __forceinline__ double2 zfma_conj(double2 a, double2 b, doub
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// right-hand-side class of p: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65+
+inline int rhs_class(int p) {
+  int c = 0;
+  while (c < 7 && p > (1 << c)) ++c;
+  return c;
+}
+
 int sm_count();
+
+// FP32 products on a handle's stored columns (products_simt.cu); warps = compute warps per CTA
+// (6 or 9, anything else 9).  X / Phi are the M-row operands (after V^H for ACA storage).
+int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, int warps, cudaStream_t st);
+int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, int warps,
+                 cudaStream_t st);
 
 // number of kernels this library has launched (all entry points), for launch accounting
 void count_launch(int n = 1);

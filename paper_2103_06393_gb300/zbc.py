@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libzbc.so")
 
 ZBC_OK, ZBC_EINVAL, ZBC_ENOMEM, ZBC_ECUDA, ZBC_ETOL, ZBC_ETIMEOUT, ZBC_ENAN, ZBC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
-FP32_SIMT, TF32X3, BF16X3 = 0, 1, 2
+FP32_SIMT, TF32X3, BF16X3, AUTO = 0, 1, 2, 3
 HOSVD, RANDOMIZED_LEARNED, RANDOMIZED_FIXED = 0, 1, 2
 ACA_DENSE_U, ACA_ALG3 = 0, 1
 PRECISIONS = {"fp32_simt": FP32_SIMT, "tf32x3": TF32X3, "bf16x3": BF16X3}
@@ -98,6 +98,7 @@ def lib():
             "zbc_rank_widths": ([vp, vp, i32, C.POINTER(zbc_grid), i32, vp, vp], i32),
             "zbc_rmatvec_noalloc": ([vp, vp, i64, i32, vp, i64, vp], i32),
             "zbc_product_status": ([vp, vp], i32),
+            "zbc_tune": ([vp, i32, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -399,6 +400,17 @@ def zbc_rmatvec_noalloc(h: Handle, Phi, Psi, stream=None):
     p = Phi.shape[0]
     _check(lib().zbc_rmatvec_noalloc(h.ptr, _ptr(Phi), _ld(Phi), p, _ptr(Psi), _ld(Psi), _stream(stream)))
     return Psi
+
+
+TUNE_VARIANTS = ("fwd_simt6", "fwd_simt9", "fwd_tf32x3", "fwd_bf16x3", "adj_simt6", "adj_simt9")
+
+
+def zbc_tune(h: Handle, p: int, stream=None) -> dict:
+    """Time the product variants for p right-hand sides and record the fastest for AUTO; returns
+    {variant: ms per call} (inf for a variant that does not fit)."""
+    t = (C.c_float * 6)()
+    _check(lib().zbc_tune(h.ptr, int(p), _stream(stream), t))
+    return dict(zip(TUNE_VARIANTS, [float(x) for x in t]))
 
 
 def zbc_product_status(h: Handle, stream=None):
