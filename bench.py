@@ -44,6 +44,22 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest_rank_ms(ms, ws, device):
+    """Max over ranks of a per-rank time: the job ends with its slowest rank."""
+    if ws == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, ms, ws):
+    """Aggregate throughput of ws replicas, each doing flops_per_rank in the job's time ms."""
+    return ws * flops_per_rank / (ms * 1e-3) / 1e12
+
+
 # ---------------------------------------------------------------------------------------------
 # workload construction on the GPU (assembly + HOSVD through the C ABI)
 # ---------------------------------------------------------------------------------------------
@@ -295,12 +311,8 @@ def run_zbc(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms = float(np.mean(times))
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * F / (ms * 1e-3) / 1e12
+    ms = slowest_rank_ms(np.mean(times), ws, "cuda")
+    value = whole_job_tflops(F, ms, ws)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(np.ascontiguousarray(X.T)).pin_memory()
@@ -319,7 +331,7 @@ def run_zbc(args):
         e2e_step()
     torch.cuda.synchronize()
     te = time_steps(e2e_step, max(3, args.steps // 2), flush, torch, stream)
-    e2e_ms = float(np.mean(te))
+    e2e_ms = slowest_rank_ms(np.mean(te), ws, "cuda")
     h2d = Xh.numel() * 8 + Phih.numel() * 8
     d2h = Yh.numel() * 8 + Psih.numel() * 8
 
@@ -373,7 +385,7 @@ def run_zbc(args):
                               for n, v in fwd.items()},
                   "adjoint": {n: {"ms": v["ms"], "rel_err": ep.get(n), "tflops": F1 / (v["ms"] * 1e-3) / 1e12}
                               for n, v in adj.items()}},
-        "e2e": {"value": ws * F / (e2e_ms * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_tflops(F, e2e_ms, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "roofline": roof,
@@ -385,6 +397,99 @@ def run_zbc(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_compression(args):
+    """Compression benchmark of the learned workload (128^3 voxels, 2 mm, 4096 random segments,
+    tol 1e-6): truncated HOSVD against the MLP-width randomized Tucker with HOSVD fallback, on the
+    same assembled columns.  The MLP is first trained on the HOSVD ranks of other columns of the
+    workload.  Prints one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_06393_gb300 import inputs, zbc
+
+    w = inputs.workload("learned")
+    g, s = w.grid, w.segments
+    ntrain, ntest, batch = 512, args.columns or 512, 128
+    perm = np.random.default_rng(7).permutation(s.m)
+    train, test = perm[:ntrain], perm[ntrain:ntrain + ntest]
+    ds = zbc.DeviceSegments(s)
+    feats_all = inputs.rank_features(g, s)
+
+    def assemble(cols):
+        cd = torch.from_numpy(np.asarray(cols, dtype=np.int32)).cuda()
+        Z = zbc.colmajor(3 * g.nv, len(cols), torch.complex64)
+        zbc.vsie_assemble_columns(g, ds, w.freq_hz, cd, Z)
+        return Z
+
+    def ranks_of(h):
+        r, _, _ = h.export()
+        return r.reshape(-1, 9)
+
+    # 1. HOSVD ranks of the training columns -> MLP targets log(rank)
+    rt = []
+    for b0 in range(0, ntrain, batch):
+        Z = assemble(train[b0:b0 + batch])
+        h, _ = zbc.tucker_compress(Z, g, w.tol)
+        rt.append(ranks_of(h))
+        del h, Z
+    T = torch.from_numpy(np.log(np.concatenate(rt).astype(np.float32))).cuda()
+    X = torch.from_numpy(feats_all[train]).cuda()
+    model = zbc.Mlp(inputs.mlp_init_params(0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = model.train(X, T, 3000, 1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    loss = hist.cpu().numpy()
+
+    # 2. the test columns, both ways
+    lmax = 64
+    sk = [zbc.to_colmajor(o) for o in inputs.mode_sketches(g, lmax, seed=11)]
+    t_h = t_r = 0.0
+    nf = nt = 0
+    err_h = err_r = 0.0
+    rk_h, rk_r, exact = [], [], 0
+    for b0 in range(0, ntest, batch):
+        cols = test[b0:b0 + batch]
+        Z = assemble(cols)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh, sh = zbc.tucker_compress(Z, g, w.tol)
+        torch.cuda.synchronize()
+        t_h += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        widths = model.widths(torch.from_numpy(feats_all[cols]).cuda(), g, oversample=4)
+        hr, sr = zbc.tucker_compress_randomized(Z, g, w.tol, widths, sk, lmax)
+        torch.cuda.synchronize()
+        t_r += time.perf_counter() - t0
+        nf += sr.n_fallback
+        nt += sr.n_tensors
+        err_h, err_r = max(err_h, sh.max_rel_err), max(err_r, sr.max_rel_err)
+        a, b = ranks_of(hh), ranks_of(hr)
+        rk_h.append(a)
+        rk_r.append(b)
+        exact += int(np.sum(np.all(a == b, axis=1)))
+        del hh, hr, Z
+    rk_h, rk_r = np.concatenate(rk_h), np.concatenate(rk_r)
+    line = {
+        "metric": "Tucker compression time per column, HOSVD vs MLP-width randomized (fallback rate)",
+        "value": 1e3 * t_r / ntest, "unit": "ms/column", "higher_is_better": False, "n_gpus": 1,
+        "data": "synthetic", "dtype": "c64 input, FP64 factorisation",
+        "config": {"workload": "learned: 128^3 voxels (2 mm), 4096 random 5 mm segments, 298.2 MHz, tol 1e-6",
+                   "train_columns": ntrain, "test_columns": ntest, "batch": batch, "sketch_lmax": lmax,
+                   "oversample": 4, "mlp_steps": 3000, "mlp_lr": 1e-3},
+        "hosvd_ms_per_column": 1e3 * t_h / ntest,
+        "randomized_ms_per_column": 1e3 * t_r / ntest,
+        "speedup": t_h / t_r if t_r > 0 else None,
+        "fallback_rate": nf / max(1, nt),
+        "max_rel_err": {"hosvd": err_h, "randomized": err_r, "tol": w.tol},
+        "mean_rank": {"hosvd": float(rk_h.mean()), "randomized": float(rk_r.mean())},
+        "columns_with_equal_ranks": exact / max(1, len(rk_h)),
+        "mlp": {"train_s": t_train, "loss_first": float(loss[0]), "loss_last": float(loss[-1])},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -437,12 +542,16 @@ def main():
     ap.add_argument("--impl", default="zbc", choices=["zbc", "reference"])
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compression", action="store_true",
+                    help="compression benchmark (HOSVD vs learned randomized Tucker) instead of the products")
     ap.add_argument("--columns", type=int, default=0,
                     help="keep only the first N segments (smaller case for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.compression:
+        run_compression(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_zbc(args)

@@ -269,3 +269,23 @@ def rank_features(grid: Grid, segs: Segments) -> np.ndarray:
     d = bbox_distance(grid, segs.centre)
     f = np.concatenate([segs.centre / LENGTH_SCALE, segs.tangent, (d / LENGTH_SCALE)[:, None]], axis=1)
     return f.astype(np.float32)
+
+
+# --------------------------------------------------------------------------------------------
+# rank-predictor initial weights
+# --------------------------------------------------------------------------------------------
+
+MLP_SIZES = (7, 64, 64, 64, 9)
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """He-uniform weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)) and zero biases for the
+    7-64-64-64-9 rank predictor, packed as float32 layer by layer: W (out x in, row-major), then b."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(len(MLP_SIZES) - 1):
+        fi, fo = MLP_SIZES[i], MLP_SIZES[i + 1]
+        lim = np.sqrt(6.0 / fi)
+        parts.append(rng.uniform(-lim, lim, size=(fo, fi)).reshape(-1))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
