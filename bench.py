@@ -233,11 +233,11 @@ def run_zbc(args):
     def flush():
         flushbuf.fill_(1)
 
-    names = {zbc.FP32_SIMT: "fp32_simt", zbc.TF32X3: "tf32x3", zbc.BF16X3: "bf16x3"}
+    names = {zbc.FP32_SIMT: "fp32_simt", zbc.TF32X3: "tf32x3", zbc.BF16X3: "bf16x3", zbc.TC2: "tc2"}
 
     def available(fn, a, b):
         out = [zbc.FP32_SIMT]
-        for code in (zbc.TF32X3, zbc.BF16X3):
+        for code in (zbc.TF32X3, zbc.BF16X3, zbc.TC2):
             try:
                 fn(h, a, b, code)
                 out.append(code)

@@ -57,11 +57,14 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  * TF32X3    : tensor cores, tcgen05 kind::tf32, each operand split hi+lo, 3 products, FP32 accumulation.
  * BF16X3    : tensor cores, tcgen05 kind::f16 with bf16 operands split into 3 terms
  *             (hi+mid+lo), the 6 products above 2^-24, FP32 accumulation.
+ * TC2       : (forward only) the last mode product of the decompression on the tensor cores
+ *             too: Z = U1 W per column as a tcgen05 MMA with fp16 hi+lo operands (W scaled by a
+ *             power of two per tensor), chained through TMEM into the BF16X3 contraction.
  * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
  *             right-hand-side class; before any tuning, BF16X3 for the forward product when
  *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,
  *             but their last bits differ, so AUTO results depend on the tuning. */
-typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2, ZBC_AUTO = 3 } zbc_precision;
+typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2, ZBC_AUTO = 3, ZBC_TC2 = 4 } zbc_precision;
 
 typedef enum { ZBC_HOSVD = 0, ZBC_RANDOMIZED_LEARNED = 1, ZBC_RANDOMIZED_FIXED = 2 } zbc_tucker_method;
 
@@ -273,11 +276,11 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
 /*
  * zbc_tune -- autotuner of the product kernels (no counterpart in the paper).  Times, on this
  * handle with p right-hand sides (zero-filled scratch operands), every variant of
- *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3
+ *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2
  *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA
  * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
  * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the adjoint's choice).
- *   times_ms_host : optional float[6], the variants' times in the order above (ms per call;
+ *   times_ms_host : optional float[7], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
  */

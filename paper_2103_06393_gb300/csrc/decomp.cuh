@@ -199,11 +199,25 @@ __device__ __forceinline__ void last_mode4(const float2* __restrict__ u1, int B1
 }
 
 // the decompression cache of a handle (built by build_decomp_cache in decomp_cache.cu)
+// U1 as the A operand of the tensor-core mode product (products_tc2.cu): per tensor and i1 tile,
+// two fp16 terms (hi, lo = x - hi) of the real embedding A1[i1][2a + e] = (Re, Im) U1[i1, a],
+// K padded to Kp1 = 8 kb1 (a multiple of 16), in the K-major core-matrix layout of tc_common.cuh
+// (rows grouped by 8, SBO = kb1 * 128); only the first RG = ceil(B1 / 8) row groups are stored.
+struct HalfDesc {
+  int64_t off;  // bytes into the fp16 block array: [t1][term][RG row groups][kb1 chunks][8 rows][16 B]
+  int kb1;      // 16-byte K chunks per row (even)
+  int wexp;     // |W| < 2^wexp: W enters the fp16 operand scaled by 2^-wexp
+};
+
 struct DecompCache {
-  float2* data = nullptr;   // W blocks and U1 row-major copies
+  float2* data = nullptr;   // W blocks and tile-blocked U1
   CacheDesc* d_desc = nullptr;
   int64_t elems = 0;
+  unsigned char* half = nullptr;  // fp16 U1 operand blocks (built on first use of the chained path)
+  HalfDesc* d_half = nullptr;
+  int kb1_max = 0;
 };
 int build_decomp_cache(Handle& h, cudaStream_t st);
+int build_half_cache(Handle& h, cudaStream_t st);
 
 }  // namespace zbc

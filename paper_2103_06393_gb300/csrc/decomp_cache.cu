@@ -7,7 +7,10 @@
 // product kernels.  Size: sum over tensors of (n2 n3 + nb1 B1p) r1p complex64.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "decomp.cuh"
+#include "tc_common.cuh"
 
 namespace zbc {
 
@@ -15,6 +18,8 @@ void cache_release(DecompCache* c) {
   if (!c) return;
   if (c->data) cudaFree(c->data);
   if (c->d_desc) cudaFree(c->d_desc);
+  if (c->half) cudaFree(c->half);
+  if (c->d_half) cudaFree(c->d_half);
   delete c;
 }
 
@@ -115,6 +120,88 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
   }
   h.cache = c;
   h.cache_r = rmax;
+  return ZBC_OK;
+}
+
+// one thread per (tensor, i1 tile, term, row r < 8 RG, chunk kc < kb1): 8 fp16 values
+__global__ void __launch_bounds__(256) build_half_kernel(const float2* __restrict__ cache,
+                                                         const CacheDesc* __restrict__ cdesc,
+                                                         const HalfDesc* __restrict__ hdesc, int ntens, int n1,
+                                                         int kb1max, unsigned char* __restrict__ out) {
+  const int B1 = tile_b1(n1), B1p = tile_b1p(n1), nb1 = (n1 + B1 - 1) / B1, RG = (B1 + 7) / 8;
+  const int t = blockIdx.y;
+  if (t >= ntens) return;
+  const CacheDesc cd = cdesc[t];
+  const HalfDesc hd = hdesc[t];
+  const int per_term = RG * 8 * hd.kb1;  // (row, chunk) items per term
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nb1 * 2 * per_term; o += gridDim.x * blockDim.x) {
+    const int t1 = o / (2 * per_term), rem = o % (2 * per_term);
+    const int term = rem / per_term, rc = rem % per_term;
+    const int r = rc / hd.kb1, kc = rc % hd.kb1;
+    const int i1 = t1 * B1 + r;
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float x2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int kk = 8 * kc + 2 * i + h, a = kk >> 1, e = kk & 1;
+        float x = 0.f;
+        if (a < cd.r1 && r < B1 && i1 < n1) {
+          const float2 u = cache[cd.uoff + ((int64_t)t1 * cd.r1p + a) * B1p + r];
+          x = e ? u.y : u.x;
+        }
+        const __half hi = __float2half_rn(x);
+        x2[h] = term == 0 ? x : x - __half2float(hi);
+      }
+      const __half2 v = __floats2half2_rn(x2[0], x2[1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+    unsigned char* dst = out + hd.off + (int64_t)t1 * 2 * RG * hd.kb1 * 128 + (int64_t)term * RG * hd.kb1 * 128 +
+                         tc::core_off(r, kc, hd.kb1);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+int build_half_cache(Handle& h, cudaStream_t st) {
+  ZBC_TRY(build_decomp_cache(h, st));
+  DecompCache* c = h.cache;
+  if (c->half) return ZBC_OK;
+  const int T = (int)h.desc.size();
+  const int B1 = tile_b1(h.n1), nb1 = (h.n1 + B1 - 1) / B1, RG = (B1 + 7) / 8;
+  std::vector<HalfDesc> hd(T);
+  int64_t off = 0;
+  int kbmax = 2;
+  for (int t = 0; t < T; ++t) {
+    const int r1p = (h.desc[t].r1 + 1) / 2 * 2;
+    hd[t].kb1 = (2 * r1p + 15) / 16 * 2;  // Kp1 = 2 r1p rounded up to 16 reals, 8 reals per chunk
+    hd[t].wexp = (int)h.desc[t].scale_log2 + 1;
+    hd[t].off = off;
+    off += (int64_t)nb1 * 2 * RG * hd[t].kb1 * 128;
+    kbmax = std::max(kbmax, hd[t].kb1);
+  }
+  cudaError_t e = cudaMalloc(&c->half, std::max<int64_t>(16, off));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_half, sizeof(HalfDesc) * std::max(1, T));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_half, hd.data(), sizeof(HalfDesc) * T, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+      const int nt = std::min(65535, T - t0);
+      build_half_kernel<<<dim3(ceil_div((int64_t)nb1 * 2 * RG * 8 * kbmax, 256), nt), 256, 0, st>>>(
+          c->data, c->d_desc + t0, c->d_half + t0, nt, h.n1, kbmax, c->half);
+      count_launch();
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    if (c->half) cudaFree(c->half);
+    if (c->d_half) cudaFree(c->d_half);
+    c->half = nullptr;
+    c->d_half = nullptr;
+    set_error("fp16 operand cache build failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
+  }
+  c->kb1_max = kbmax;
   return ZBC_OK;
 }
 

@@ -7,6 +7,7 @@
 namespace zbc {
 int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, zbc_precision prec,
               cudaStream_t st);
+int matvec_tc2(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
 int aca_pre(const Handle& h, const float2* X, int64_t ldx, int p, float2* Xp, cudaStream_t st);
 int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ldpsi, cudaStream_t st);
 
@@ -22,6 +23,7 @@ static int matvec_impl(Handle& h, const float2* X, int64_t ldx, int p, float2* Y
     ldxe = h.M;
   }
   if (prec == ZBC_FP32_SIMT) return matvec_simt(h, Xe, ldxe, p, Y, ldy, warps, st);
+  if (prec == ZBC_TC2) return matvec_tc2(h, Xe, ldxe, p, Y, ldy, st);
   return matvec_tc(h, Xe, ldxe, p, Y, ldy, prec, st);
 }
 
@@ -50,7 +52,8 @@ extern "C" int zbc_matvec(const zbc_handle* hh, const void* X, int64_t ldx, int 
   ZBC_CHECK_ARG(p >= 1 && p <= 1024, "p must be in [1, 1024] (got %d)", p);
   ZBC_CHECK_ARG(ldx >= h.m, "ldx (%lld) < m (%d)", (long long)ldx, h.m);
   ZBC_CHECK_ARG(ldy >= (int64_t)h.q * h.nv(), "ldy < q*n_v");
-  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO,
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
+                    prec == ZBC_TC2,
                 "unknown precision %d", (int)prec);
   const int cls = rhs_class(p);
   int warps = h.tune_fwd_warps[cls];
@@ -67,7 +70,8 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   ZBC_CHECK_ARG(p >= 1 && p <= 1024, "p must be in [1, 1024] (got %d)", p);
   ZBC_CHECK_ARG(ldphi >= (int64_t)h.q * h.nv(), "ldphi < q*n_v");
   ZBC_CHECK_ARG(ldpsi >= h.m, "ldpsi (%lld) < m (%d)", (long long)ldpsi, h.m);
-  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO,
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
+                    prec == ZBC_TC2,
                 "unknown precision %d", (int)prec);
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_AUTO,
                 "the adjoint product has no tensor-core form: use ZBC_FP32_SIMT or ZBC_AUTO");
@@ -97,11 +101,13 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
     zbc_precision prec;
     int warps;
   };
-  const Variant vars[6] = {{true, ZBC_FP32_SIMT, 6}, {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
-                           {true, ZBC_BF16X3, 0},    {false, ZBC_FP32_SIMT, 6}, {false, ZBC_FP32_SIMT, 9}};
-  float t[6];
+  constexpr int NV = 7;
+  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6}, {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
+                            {true, ZBC_BF16X3, 0},    {true, ZBC_TC2, 0},         {false, ZBC_FP32_SIMT, 6},
+                            {false, ZBC_FP32_SIMT, 9}};
+  float t[NV];
   int status = ZBC_OK;
-  for (int i = 0; i < 6 && status == ZBC_OK; ++i) {
+  for (int i = 0; i < NV && status == ZBC_OK; ++i) {
     const Variant& v = vars[i];
     auto run = [&]() {
       return v.fwd ? matvec_impl(h, (const float2*)X.ptr, h.m, p, (float2*)Y.ptr, rows, v.prec, v.warps, st)
@@ -132,15 +138,15 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   cudaEventDestroy(e1);
   if (status != ZBC_OK) return status;
   const int cls = rhs_class(p);
-  int bf = 0, ba = 4;
-  for (int i = 1; i < 4; ++i)
+  int bf = 0, ba = 5;
+  for (int i = 1; i < 5; ++i)
     if (t[i] < t[bf]) bf = i;
-  if (t[5] < t[4]) ba = 5;
+  if (t[6] < t[5]) ba = 6;
   h.tune_fwd_prec[cls] = (int8_t)vars[bf].prec;
   h.tune_fwd_warps[cls] = (int8_t)vars[bf].warps;
   h.tune_adj_warps[cls] = (int8_t)vars[ba].warps;
   if (times_ms_host)
-    for (int i = 0; i < 6; ++i) times_ms_host[i] = t[i];
+    for (int i = 0; i < NV; ++i) times_ms_host[i] = t[i];
   return ZBC_OK;
 }
 

@@ -1,4 +1,5 @@
-"""Tensor-core products (tcgen05, TF32X3 and BF16X3 splits) against the FP64 oracle on the same
+"""Tensor-core products (tcgen05: TF32X3 and BF16X3 contractions, and TC2 with the mode product
+on the tensor cores too) against the FP64 oracle on the same
 compressed data: several RHS counts (padding of the RHS chunk), ragged tiles, ACA storage."""
 import numpy as np
 import pytest
@@ -18,7 +19,7 @@ __graft_entry__.build()
 from paper_2103_06393_gb300 import zbc  # noqa: E402
 
 RTOL = 1e-5
-TC = [zbc.TF32X3, zbc.BF16X3]
+TC = [zbc.TF32X3, zbc.BF16X3, zbc.TC2]
 
 
 def rel_cols(a, b):
