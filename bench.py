@@ -492,6 +492,96 @@ def run_compression(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batching(args):
+    """Batching benchmark of the ACA workload (160 x 160 x 128 voxels at 1.5 mm, 16 loops x 256
+    segments, ACA tol 1e-6, Tucker 3e-6): for p = 1 .. 128 right-hand sides, the tuned forward and
+    adjoint products (ZBC_AUTO after zbc_tune), then the whole mixed batch (one product pair per
+    p) eagerly and as one replayed CUDA graph.  Prints one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_06393_gb300 import inputs, zbc
+
+    w = inputs.workload("batching")
+    g, s = w.grid, w.segments
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, ast, piv = zbc.aca_compress(g, zbc.DeviceSegments(s), w.freq_hz, w.tol, 400, zbc.ACA_DENSE_U)
+    torch.cuda.synchronize()
+    t_aca = time.perf_counter() - t0
+    inf = h.info()
+    ranks, _, _ = h.export()
+    r = np.asarray(ranks, dtype=np.float64).reshape(-1, 3)
+    n1, n2, n3 = g.shape
+    nv = n1 * n2 * n3
+    dec = float((n1 * r[:, 0] * r[:, 1] * r[:, 2] + n1 * n2 * r[:, 1] * r[:, 2] + nv * r[:, 2]).sum())
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ps = [1, 2, 4, 8, 16, 32, 64, 128]
+    per_p, bufs = {}, []
+    for p in ps:
+        F = 2 * (8.0 * dec + 8.0 * 3 * nv * inf.M * p + 8.0 * inf.M * inf.m * p)
+        X = zbc.to_colmajor(inputs.cn01((inf.m, p), seed=p).astype(np.complex64))
+        Phi = zbc.to_colmajor(inputs.cn01((3 * nv, p), seed=100 + p).astype(np.complex64))
+        Y = zbc.colmajor(3 * nv, p, torch.complex64)
+        Psi = zbc.colmajor(inf.m, p, torch.complex64)
+        tune = zbc.zbc_tune(h, p)
+
+        def pair(X=X, Y=Y, Phi=Phi, Psi=Psi):
+            zbc.zbc_matvec(h, X, Y, zbc.AUTO)
+            zbc.zbc_rmatvec(h, Phi, Psi, zbc.AUTO)
+
+        for _ in range(3):
+            pair()
+        ms = statistics.median(time_steps(pair, 5, lambda: flush.fill_(1), torch, stream))
+        fv = min((k for k in tune if k.startswith("fwd_")), key=lambda k: tune[k])
+        per_p[str(p)] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "forward": fv,
+                         "fwd_ms": tune[fv], "adj_ms": min(tune["adj_simt6"], tune["adj_simt9"])}
+        bufs.append(pair)
+        log(f"[bench] batching p={p}: {ms:.3f} ms ({per_p[str(p)]['tflops']:.1f} TFLOP/s, {fv})")
+
+    def mixed():
+        for f in bufs:
+            f()
+
+    for _ in range(2):
+        mixed()
+    torch.cuda.synchronize()
+    eager = statistics.median(time_steps(mixed, 3, lambda: flush.fill_(1), torch, stream))
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        mixed()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        mixed()
+    graph.replay()
+    torch.cuda.synchronize()
+    replay = statistics.median(time_steps(graph.replay, 3, lambda: flush.fill_(1), torch, stream))
+    zbc.zbc_product_status(h)
+    Ftot = sum(v["tflops"] * v["ms"] * 1e-3 * 1e12 for v in per_p.values())
+    line = {
+        "metric": "mixed-batch Z x and Z^H v throughput (p = 1..128), ACA storage, graph-captured",
+        "value": Ftot / (replay * 1e-3) / 1e12, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1,
+        "data": "synthetic", "dtype": "c64",
+        "config": {"workload": "batching: 160x160x128 voxels (1.5 mm, masked beyond r = 0.157 m), 16 loops x 256 "
+                               "segments, ACA tol 1e-6 (dense U, Tucker 3e-6)", "rhs": ps,
+                   "l2": "flushed (256 MiB write) between steps"},
+        "aca": {"rank": int(ast.rank), "converged": int(ast.converged), "seconds": t_aca, "M": inf.M,
+                "max_tucker_rank": inf.max_rank},
+        "per_p": per_p,
+        "mixed_batch_ms": {"eager": eager, "graph": replay},
+        "gpu_launches_per_batch": None,
+    }
+    l0 = zbc.kernel_launches()
+    mixed()
+    torch.cuda.synchronize()
+    line["gpu_launches_per_batch"] = zbc.kernel_launches() - l0
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -544,6 +634,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compression", action="store_true",
                     help="compression benchmark (HOSVD vs learned randomized Tucker) instead of the products")
+    ap.add_argument("--batching", action="store_true",
+                    help="mixed right-hand-side batches on the ACA workload (tuned forms, CUDA graph)")
     ap.add_argument("--columns", type=int, default=0,
                     help="keep only the first N segments (smaller case for profiler captures)")
     args = ap.parse_args()
@@ -551,6 +643,8 @@ def main():
         args.warmup = 3
     if args.compression:
         run_compression(args)
+    elif args.batching:
+        run_batching(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -137,6 +137,11 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != ZBC_OK) return status;
+  if (!(t[0] < INFINITY || t[1] < INFINITY || t[2] < INFINITY || t[3] < INFINITY || t[4] < INFINITY) ||
+      !(t[5] < INFINITY || t[6] < INFINITY)) {
+    set_error("zbc_tune: no product form fits this handle");
+    return ZBC_EINVAL;
+  }
   const int cls = rhs_class(p);
   int bf = 0, ba = 5;
   for (int i = 1; i < 5; ++i)

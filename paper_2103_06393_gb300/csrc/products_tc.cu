@@ -18,14 +18,16 @@
 // kFlush chunks and is added, with round-to-nearest FP32 on the CUDA cores, into a second TMEM
 // region S; Y = S + D at the end.
 //
-// Warp roles: a copy warp streams each column's U1 / W blocks into the stage ring of stage.cuh
+// Warp roles: a copy warp streams each column's U1 / W blocks into the stage rings of stage.cuh
 // (cp.async.bulk); the front-end ("producer") warps form the last mode product of one task of
 // the tile from the staged blocks and fill the operands of a chunk -- two warps per task, one
-// for each half of the chunk's columns, so that more warps hide the shared-memory latency;
-// one more warp issues the MMAs.  Two operand buffers alternate; an mbarrier "full" per buffer (one arrival
-// per producer warp) hands a filled buffer to the issuer, and tcgen05.commit on an mbarrier
-// "empty" per buffer hands it back once the tensor cores have consumed it.  No CTA-wide barrier
-// is taken between the prologue and the epilogue.
+// for each half of the chunk's columns (pairs interleaved), so that more warps hide the
+// shared-memory latency; one more warp issues the MMAs.  Each half has its own stage ring: a
+// ring shared by halves that consume different columns would let a fast half wait on a slot two
+// phases behind, where an mbarrier parity test cannot tell the phases apart.  One operand buffer:
+// an mbarrier "full" (one arrival per producer warp) hands the chunk's filled operands to the
+// issuer, and tcgen05.commit on an mbarrier "empty" hands them back once the tensor cores have
+// consumed them.  No CTA-wide barrier is taken between the prologue and the epilogue.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -123,6 +125,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ volatile int abort_flag;
   unsigned char* stages = smem;
   unsigned char* ops = (unsigned char*)(((uintptr_t)(smem + (size_t)S * SL.stride) + 1023) & ~(uintptr_t)1023);
+  // two rings of Sh = S / 2 stages, one per producer half: each ring is consumed in order by all
+  // of its consumers, so no waiter can run two phases ahead of a slot (parity waits stay exact)
+  const int Sh = S / 2;
   // one operand buffer: a chunk's operands are written once the previous chunk's MMAs are done
   // (the wait comes after the first columns' last mode products, so it rarely blocks), which
   // leaves shared memory for a deeper stage ring
@@ -169,9 +174,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         d.uoff = __shfl_sync(0xffffffffu, mine.uoff, i);
         d.r1 = __shfl_sync(0xffffffffu, mine.r1, i);
         d.r1p = __shfl_sync(0xffffffffu, mine.r1p, i);
-        const int c = c0 + i, st = c % S;
+        // column c goes to the ring of the half that consumes it (slots h * Sh .. h * Sh + Sh - 1),
+        // as that half's n-th column
+        const int c = c0 + i, h = (c >> 1) & 1, n = (c >> 2) * 2 + (c & 1), st = h * Sh + n % Sh;
         bool bad = false;
-        if (lane == 0 && c >= S) bad = abort_flag || !tc::mbar_wait(&sempty[st], ((c / S) - 1) & 1);
+        if (lane == 0 && n >= Sh) bad = abort_flag || !tc::mbar_wait(&sempty[st], ((n / Sh) - 1) & 1);
         if (__shfl_sync(0xffffffffu, bad, 0)) {
           if (lane == 0) abort_flag = 1;
           break;
@@ -183,7 +190,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     if (lane == 0 && abort_flag)  // let the copies in flight land before the CTA exits
-      for (int c = std::max(0, issued - S); c < issued; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
+      for (int c = std::max(0, issued - 2 * Sh - 2); c < issued; ++c) {
+        const int h = (c >> 1) & 1, n = (c >> 2) * 2 + (c & 1);
+        tc::mbar_wait(&sfull[h * Sh + n % Sh], (n / Sh) & 1);
+      }
   } else if (warp == L.nprodw + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -296,9 +306,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int l = 0; l < kUQ; ++l) zz[l] = make_float2(0.f, 0.f);
             if (jj < jc) {
-              const int c = j0 + jj, st = c % S;
+              const int c = j0 + jj, n = (c >> 2) * 2 + (c & 1), st = half * Sh + n % Sh;
               const bool ab = __any_sync(0xffffffffu, abort_flag != 0);
-              if (!ab && __all_sync(0xffffffffu, tc::mbar_wait(&sfull[st], (c / S) & 1))) {
+              if (!ab && __all_sync(0xffffffffu, tc::mbar_wait(&sfull[st], (n / Sh) & 1))) {
                 const unsigned char* sb = stages + (size_t)st * SL.stride;
                 last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0,
                                  zz);
@@ -439,13 +449,17 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
     SL = StageLayout::make(R, B1p, g.NUp, 0, 0);
     const size_t ops = 1024 + (size_t)F::terms * (L.a_bytes + L.b_bytes);
     if (ops + 2 * (size_t)SL.stride > budget) continue;
-    S = (int)std::min<size_t>(kMaxStages, (budget - ops) / SL.stride);
+    S = (int)std::min<size_t>(kMaxStages, (budget - ops) / SL.stride) / 2 * 2;
+    if (S < 4) {  // each producer half needs a ring of two stages at least
+      S = 0;
+      continue;
+    }
     sm = (size_t)S * SL.stride + ops;
   }
   int cols = 32;
   while (cols < 2 * L.nmt * P2) cols <<= 1;
   L.tmem_cols = cols;
-  if (S < 2 || cols > 512) {
+  if (S < 4 || cols > 512) {
     set_error("tensor-core layout does not fit (rank %d, tmem %d)", R, cols);
     return ZBC_EINVAL;
   }

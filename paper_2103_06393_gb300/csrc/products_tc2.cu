@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
       const int r1p = wx_r1p[st], kb1 = wx_kb1[st];
       const float sc = ldexpf(1.f, -wx_wexp[st]);
       const float2* Ws = (const float2*)(smem + L.wx + (size_t)st * L.wx_slot);
-      if (r < 16 * kb1) {
-        const int n = r / kb1, kc = r % kb1;
+      for (int it = r; it < 16 * kb1; it += 128) {  // (row, 16-byte chunk) items
+        const int n = it / kb1, kc = it % kb1;
         const int u = n >> 1, f = n & 1;
         uint32_t hi[4], lo[4];
 #pragma unroll

@@ -86,3 +86,41 @@ def test_tc_matvec_aca_storage(prec):
     h, tens = _handle(w, 1e-6, V=V)
     Y, Yo = _fwd(h, w, tens, 3, prec, V=V)
     assert rel_cols(Y, Yo).max() < RTOL
+
+
+@pytest.mark.parametrize("prec", [zbc.FP32_SIMT] + TC)
+def test_high_ranks_up_to_64(prec):
+    # ACA's U columns reach Tucker ranks far above the Green's-function columns' (r1 up to 64):
+    # random tensors with r1 in [33, 64] on a 70 x 20 x 6 grid, both products
+    rng = np.random.default_rng(21)
+    n = (70, 20, 6)
+    tens = []
+    for _ in range(10):
+        tj = []
+        for _k in range(3):
+            r = (int(rng.integers(33, 65)), int(rng.integers(1, 9)), int(rng.integers(1, 7)))
+            G = rng.normal(size=r) + 1j * rng.normal(size=r)
+            Us = [np.linalg.qr(rng.normal(size=(ni, ri)) + 1j * rng.normal(size=(ni, ri)))[0] for ni, ri in zip(n, r)]
+            tj.append((G.astype(np.complex64).astype(np.complex128),
+                       [U.astype(np.complex64).astype(np.complex128) for U in Us]))
+        tens.append(tj)
+    grid = inputs.Grid(*n, 0.002)
+    h = zbc.zbc_create_from_host(grid, 3, tens)
+    p = 12
+    X = inputs.cn01((10, p), seed=5).astype(np.complex64)
+    Y = zbc.colmajor(3 * grid.nv, p, torch.complex64)
+    try:
+        zbc.zbc_matvec(h, zbc.to_colmajor(X), Y, prec)
+    except zbc.ZbcError as e:
+        # TC2's shared-memory layout holds mode-product operands up to r1 ~ 40 only; beyond
+        # that it must refuse cleanly (the autotuner then skips it)
+        assert prec == zbc.TC2 and e.status == zbc.ZBC_EINVAL and "does not fit" in str(e)
+        return
+    zbc.zbc_product_status(h)
+    assert rel_cols(zbc.from_colmajor(Y), products.matvec(tens, n, X)).max() < RTOL
+    if prec == zbc.FP32_SIMT:
+        Phi = inputs.cn01((3 * grid.nv, p), seed=6).astype(np.complex64)
+        Psi = zbc.colmajor(10, p, torch.complex64)
+        zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
+        zbc.zbc_product_status(h)
+        assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, n, Phi)).max() < RTOL
