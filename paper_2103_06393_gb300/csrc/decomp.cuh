@@ -91,10 +91,17 @@ inline Geo make_geo(int n1, int n2, int n3, int R, int max_tasks, int max_rows =
 // two fp16 terms (hi, lo = x - hi) of the real embedding A1[i1][2a + e] = (Re, Im) U1[i1, a],
 // K padded to Kp1 = 8 kb1 (a multiple of 16), in the K-major core-matrix layout of tc_common.cuh
 // (rows grouped by 8, SBO = kb1 * 128); only the first RG = ceil(B1 / 8) row groups are stored.
+// Both fp16 operands are brought to magnitudes below 2^kHalfShift by powers of two (U1 by
+// 2^(kHalfShift - uexp), |U1| < 2^uexp; W by 2^(kHalfShift - wexp), |W| < 2^wexp) so that
+// their lo terms (~2^-11 of the value) stay normal fp16 numbers; products carry
+// 2^(2 kHalfShift - uexp - wexp), removed exactly from the FP32 result.
+constexpr int kHalfShift = 10;
+
 struct HalfDesc {
   int64_t off;  // bytes into the fp16 block array: [t1][term][RG row groups][kb1 chunks][8 rows][16 B]
   int kb1;      // 16-byte K chunks per row (even)
-  int wexp;     // |W| < 2^wexp: W enters the fp16 operand scaled by 2^-wexp
+  int wexp;     // |W| < 2^wexp
+  int uexp;     // |U1| < 2^uexp (set on the device by the cache build)
 };
 
 struct DecompCache {

@@ -123,6 +123,30 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
   return ZBC_OK;
 }
 
+// uexp of each tensor: the smallest e with |Re U1|, |Im U1| < 2^e (0 for a zero factor)
+__global__ void __launch_bounds__(256) u1_exp_kernel(const float2* __restrict__ pool,
+                                                     const TensorDesc* __restrict__ desc, int n1,
+                                                     HalfDesc* __restrict__ hdesc) {
+  const int t = blockIdx.x;
+  const TensorDesc d = desc[t];
+  const float2* U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3;
+  float m = 0.f;
+  for (int64_t o = threadIdx.x; o < (int64_t)n1 * d.r1; o += blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(U1[o].x), fabsf(U1[o].y)));
+  __shared__ float red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int e = 0;
+    if (red[0] > 0.f) frexpf(red[0], &e);  // red[0] = f 2^e with f in [0.5, 1): red[0] < 2^e
+    hdesc[t].uexp = e;
+  }
+}
+
 // one thread per (tensor, i1 tile, term, row r < 8 RG, chunk kc < kb1): 8 fp16 values
 __global__ void __launch_bounds__(256) build_half_kernel(const float2* __restrict__ cache,
                                                          const CacheDesc* __restrict__ cdesc,
@@ -149,7 +173,7 @@ __global__ void __launch_bounds__(256) build_half_kernel(const float2* __restric
         float x = 0.f;
         if (a < cd.r1 && r < B1 && i1 < n1) {
           const float2 u = cache[cd.uoff + ((int64_t)t1 * cd.r1p + a) * B1p + r];
-          x = e ? u.y : u.x;
+          x = ldexpf(e ? u.y : u.x, kHalfShift - hd.uexp);
         }
         const __half hi = __float2half_rn(x);
         x2[h] = term == 0 ? x : x - __half2float(hi);
@@ -176,6 +200,7 @@ int build_half_cache(Handle& h, cudaStream_t st) {
     const int r1p = (h.desc[t].r1 + 1) / 2 * 2;
     hd[t].kb1 = (2 * r1p + 15) / 16 * 2;  // Kp1 = 2 r1p rounded up to 16 reals, 8 reals per chunk
     hd[t].wexp = (int)h.desc[t].scale_log2 + 1;
+    hd[t].uexp = 0;
     hd[t].off = off;
     off += (int64_t)nb1 * 2 * RG * hd[t].kb1 * 128;
     kbmax = std::max(kbmax, hd[t].kb1);
@@ -184,6 +209,11 @@ int build_half_cache(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_half, sizeof(HalfDesc) * std::max(1, T));
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_half, hd.data(), sizeof(HalfDesc) * T, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+      const int nt = std::min(65535, T - t0);
+      u1_exp_kernel<<<nt, 256, 0, st>>>(h.d_pool, h.d_desc + t0, h.n1, c->d_half + t0);
+      count_launch();
+    }
     for (int t0 = 0; t0 < T; t0 += 65535) {
       const int nt = std::min(65535, T - t0);
       build_half_kernel<<<dim3(ceil_div((int64_t)nb1 * 2 * RG * 8 * kbmax, 256), nt), 256, 0, st>>>(

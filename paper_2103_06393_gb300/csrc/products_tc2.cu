@@ -6,8 +6,9 @@
 //      padded to 16: the real embedding A1[i1][2a + e] = (Re, Im) U1, and
 //        B1[2u][2a] = Re W, B1[2u][2a+1] = -Im W, B1[2u+1][2a] = Im W, B1[2u+1][2a+1] = Re W;
 //      operands split into two fp16 terms (hi, lo = x - hi; products hh, hl, lh), U1 pre-split in
-//      the handle's cache, W split per column and scaled by 2^-wexp (|W| < 2^wexp) so that it
-//      fits fp16's range, the result scaled back exactly;
+//      the handle's cache, W split per column after scaling by 2^-wexp (|W| < 2^wexp), both
+//      operands scaled by 2^kHalfShift so their lo terms stay normal fp16 numbers, the result
+//      scaled back exactly;
 //   2. the contraction Y[(i1, u), s] += sum_j Z[i1, u, j] X[j, s] over chunks of 8 columns, as in
 //      products_tc.cu: A2 = the chunk's Z (rows (u, i1), K = 16 reals), B2 = the chunk's X, bf16
 //      split in 3 terms (6 products), D2 in TMEM folded every kFlush2 chunks into a second TMEM
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t a1full[kMaxStages], a1empty[kMaxStages], wxfull[kS2], wxempty[kS2];
   __shared__ uint64_t b1full[kB1], b1empty[kB1], d1full[kB1], d1empty[kB1], a2full, a2empty;
-  __shared__ int a1_kb1[kMaxStages], wx_r1p[kS2], wx_kb1[kS2], wx_wexp[kS2];
+  __shared__ int a1_kb1[kMaxStages], wx_r1p[kS2], wx_kb1[kS2], wx_wexp[kS2], wx_uexp[kS2];
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_flag;
   const uint32_t sbase = tc::smem_u32(smem);
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
         const int64_t hoff = __shfl_sync(0xffffffffu, mh.off, i);
         const int kb1 = __shfl_sync(0xffffffffu, mh.kb1, i);
         const int wexp = __shfl_sync(0xffffffffu, mh.wexp, i);
+        const int uexp = __shfl_sync(0xffffffffu, mh.uexp, i);
         const int c = c0 + i, st = c % SR;
         bool bad = false;
         if (lane == 0 && c >= SR)
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
             wx_r1p[st] = r1p;
             wx_kb1[st] = kb1;
             wx_wexp[st] = wexp;
+            wx_uexp[st] = uexp;
             unsigned char* dst = smem + L.wx + (size_t)st * L.wx_slot;
             const uint32_t wb = 8u * nu * r1p;
             const uint32_t xb = StageLayout::r16(8u * P);
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
       if (!ok) return false;
       tc::fence_after();
       const int r1p = wx_r1p[st], kb1 = wx_kb1[st];
-      const float sc = ldexpf(1.f, -wx_wexp[st]);
+      const float sc = ldexpf(1.f, kHalfShift - wx_wexp[st]);
       const float2* Ws = (const float2*)(smem + L.wx + (size_t)st * L.wx_slot);
       for (int it = r; it < 16 * kb1; it += 128) {  // (row, 16-byte chunk) items
         const int n = it / kb1, kc = it % kb1;
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
         const int cn = col(n + kAhead);
         if (cn < M && !(good = build_b1(cn))) continue;
         const unsigned char* sb = smem + L.wx + (size_t)st * L.wx_slot;
-        const float zs = ldexpf(1.f, wx_wexp[st]);
+        const float zs = ldexpf(1.f, wx_wexp[st] + wx_uexp[st] - 2 * kHalfShift);
         if (r < P2) {
           const float2 xv = ((const float2*)(sb + L.wx_x))[r >> 1];
           const int eo = r & 1;

@@ -124,3 +124,13 @@ def test_high_ranks_up_to_64(prec):
         zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
         zbc.zbc_product_status(h)
         assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, n, Phi)).max() < RTOL
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_tc_long_i1_many_columns(prec):
+    # n1 = 96 as in the 96^3 workload (U1 entries ~ 0.1, whose fp16 lo terms would fall below
+    # fp16's normal range without scaling) and 256 columns (32 chunks: eight folds of D)
+    w = inputs.scaled_workload("precision", (96, 10, 8), m=256)
+    h, tens = _handle(w, 1e-6)
+    Y, Yo = _fwd(h, w, tens, 16, prec, seed=9)
+    assert rel_cols(Y, Yo).max() < RTOL
