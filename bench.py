@@ -359,6 +359,16 @@ def run_zbc(args):
         roof = {"bound": "tensor", "achieved": F1 / (dom_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"measured bf16 {bf} TFLOP/s / 6 real products per complex-split MAC",
                 "kernel": kern, "traffic": None}
+    # DRAM bytes per launch of the dominant kernel on this workload, from a one-pass ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; only for the full workload
+    # and the kernel version it was taken on
+    measured_traffic = {("rmatvec_simt_kernel", "adj_simt9"): 3.313e9 + 0.059e9,
+                        ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9,
+                        ("matvec_tc_kernel", "fwd_tf32x3"): 2.907e9 + 0.327e9,
+                        ("matvec_tc_kernel", "fwd_bf16x3"): 2.871e9 + 0.327e9}
+    dom_variant = variant["forward"] if dom_fwd else variant["adjoint"]
+    if not args.columns:
+        roof["traffic"] = measured_traffic.get((kern, dom_variant))
     roof["frac"] = roof["achieved"] / roof["peak"]
 
     cpu = None
