@@ -363,9 +363,7 @@ def run_zbc(args):
     # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; only for the full workload
     # and the kernel version it was taken on
     measured_traffic = {("rmatvec_simt_kernel", "adj_simt9"): 3.313e9 + 0.059e9,
-                        ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9,
-                        ("matvec_tc_kernel", "fwd_tf32x3"): 2.907e9 + 0.327e9,
-                        ("matvec_tc_kernel", "fwd_bf16x3"): 2.871e9 + 0.327e9}
+                        ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9}
     dom_variant = variant["forward"] if dom_fwd else variant["adjoint"]
     if not args.columns:
         roof["traffic"] = measured_traffic.get((kern, dom_variant))

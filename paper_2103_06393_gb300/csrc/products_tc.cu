@@ -18,7 +18,7 @@
 // kFlush chunks and is added, with round-to-nearest FP32 on the CUDA cores, into a second TMEM
 // region S; Y = S + D at the end.
 //
-// Warp roles: a copy warp streams each column's U1 / W blocks into the stage rings of stage.cuh
+// Warp roles: two copy warps stream each column's U1 / W blocks into the stage rings of stage.cuh
 // (cp.async.bulk); the front-end ("producer") warps form the last mode product of one task of
 // the tile from the staged blocks and fill the operands of a chunk -- two warps per task, one
 // for each half of the chunk's columns (pairs interleaved), so that more warps hide the
@@ -38,7 +38,7 @@ namespace zbc {
 
 constexpr int kFlush = 4;       // chunks accumulated in D before it is folded into S
 constexpr int kTcMaxTasks = 6;  // tasks per tile, at most (two producer warps each)
-constexpr int kTcThreads = 32 * (2 * kTcMaxTasks + 2);  // + the copy warp and the MMA issuer
+constexpr int kTcThreads = 32 * (2 * kTcMaxTasks + 3);  // + a copy warp per half and the MMA issuer
 
 struct TcPack {
   int dummy;
@@ -160,9 +160,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem_s = tbase + (uint32_t)(L.nmt * P2);  // S: nmt * P2 columns
   const int nchunks = (M + kChunk - 1) / kChunk;
 
-  if (warp == L.nprodw) {
-    // ---------------- copy warp: the columns' U1 / W blocks into the stage ring ----------------
+  if (warp == L.nprodw || warp == L.nprodw + 1) {
+    // ---------------- copy warps, one per half: its columns' U1 / W blocks into its ring ----------------
     // lane l holds the cache entry of column c0 + l of the current batch of 32 columns
+    const int hw = warp - L.nprodw;  // the half this warp feeds
     int issued = 0;
     for (int c0 = 0; c0 < M && !__any_sync(0xffffffffu, abort_flag != 0); c0 += 32) {
       CacheDesc mine{};
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // column c goes to the ring of the half that consumes it (slots h * Sh .. h * Sh + Sh - 1),
         // as that half's n-th column
         const int c = c0 + i, h = (c >> 1) & 1, n = (c >> 2) * 2 + (c & 1), st = h * Sh + n % Sh;
+        if (h != hw) continue;
         bool bad = false;
         if (lane == 0 && n >= Sh) bad = abort_flag || !tc::mbar_wait(&sempty[st], ((n / Sh) - 1) & 1);
         if (__shfl_sync(0xffffffffu, bad, 0)) {
@@ -192,9 +194,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0 && abort_flag)  // let the copies in flight land before the CTA exits
       for (int c = std::max(0, issued - 2 * Sh - 2); c < issued; ++c) {
         const int h = (c >> 1) & 1, n = (c >> 2) * 2 + (c & 1);
-        tc::mbar_wait(&sfull[h * Sh + n % Sh], (n / Sh) & 1);
+        if (h == hw) tc::mbar_wait(&sfull[h * Sh + n % Sh], (n / Sh) & 1);
       }
-  } else if (warp == L.nprodw + 1) {
+  } else if (warp == L.nprodw + 2) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::instr_desc(128, P2, F::idfmt);
@@ -473,7 +475,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
     attr_set = true;
   }
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
-  matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 2), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL,
+  matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 3), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL,
                                                                    S, L, XT, pst, p, Y, ldy, (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
