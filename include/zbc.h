@@ -131,7 +131,9 @@ int vsie_assemble_columns(const zbc_grid* g, const zbc_segments* s, double freq_
 /*
  * tucker_compress -- column-wise Tucker compression (Sec. III.A, Fig. 2; truncated HOSVD of
  * Sec. II.B.1 with De Lathauwer's bound).
- *   cols   : device, (q*n_v) x ncols column-major (ld >= q*n_v), dtype in_dt
+ *   cols   : device, (q*n_v) x ncols column-major (ld >= q*n_v), dtype in_dt; q = 1 .. 12
+ *            components per column (3: the point-matched piecewise-constant kernel; 12: a
+ *            piecewise-linear basis, whose column assembly this library does not provide)
  *   tol    : per-tensor relative Frobenius tolerance; mode g keeps the smallest r_g with
  *            sum_{i>r_g} sigma_i^2 <= (tol^2/3) ||A||_F^2 (so ||A - A~||_F <= tol ||A||_F)
  *   method : ZBC_HOSVD (FP64 two-pass Gram + Jacobi eigensolver per unfolding), or one of the

@@ -198,7 +198,7 @@ static int validate_grid(const zbc_grid* g, int q) {
   ZBC_CHECK_ARG(g->n1 >= 2 && g->n2 >= 2 && g->n3 >= 2 && g->n1 <= 4096 && g->n2 <= 4096 && g->n3 <= 4096,
                 "grid sizes must be in [2, 4096] (got %d %d %d)", g->n1, g->n2, g->n3);
   ZBC_CHECK_ARG(g->h > 0 && std::isfinite(g->h), "grid spacing must be positive");
-  ZBC_CHECK_ARG(q == 3, "q must be 3 (piecewise-constant basis)");
+  ZBC_CHECK_ARG(q >= 1 && q <= 12, "q must be in [1, 12] (3: piecewise-constant basis, 12: piecewise-linear)");
   return ZBC_OK;
 }
 

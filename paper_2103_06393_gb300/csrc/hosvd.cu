@@ -1217,7 +1217,7 @@ static int finish_compress(zbc_handle** out, const zbc_grid* g, int q, int ncols
 static int check_compress_args(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
                                double tol, zbc_handle** out) {
   ZBC_CHECK_ARG(cols && g && out, "tucker_compress: null argument");
-  ZBC_CHECK_ARG(q == 3, "q must be 3");
+  ZBC_CHECK_ARG(q >= 1 && q <= 12, "q must be in [1, 12]");
   ZBC_CHECK_ARG(g->n1 >= 2 && g->n2 >= 2 && g->n3 >= 2 && g->n1 <= 1024 && g->n2 <= 1024 && g->n3 <= 1024,
                 "grid sizes must be in [2, 1024]");
   ZBC_CHECK_ARG(g->n1 % 2 == 0 && g->n2 % 2 == 0 && g->n3 % 2 == 0, "grid sizes must be even");
@@ -1262,7 +1262,7 @@ extern "C" int tucker_compress(const void* cols, int64_t ld, int ncols, const zb
   ZBC_CHECK_ARG(method == ZBC_HOSVD,
                 "the randomized methods take widths and sketches: use tucker_compress_randomized");
   ZBC_CHECK_ARG(cols && g && out, "tucker_compress: null argument");
-  ZBC_CHECK_ARG(q == 3, "q must be 3");
+  ZBC_CHECK_ARG(q >= 1 && q <= 12, "q must be in [1, 12]");
   ZBC_CHECK_ARG(g->n1 >= 2 && g->n2 >= 2 && g->n3 >= 2 && g->n1 <= 1024 && g->n2 <= 1024 && g->n3 <= 1024,
                 "grid sizes must be in [2, 1024]");
   ZBC_CHECK_ARG(g->n1 % 2 == 0 && g->n2 % 2 == 0 && g->n3 % 2 == 0, "grid sizes must be even");

@@ -134,3 +134,61 @@ def test_tc_long_i1_many_columns(prec):
     h, tens = _handle(w, 1e-6)
     Y, Yo = _fwd(h, w, tens, 16, prec, seed=9)
     assert rel_cols(Y, Yo).max() < RTOL
+
+
+@pytest.mark.parametrize("prec", [zbc.FP32_SIMT, zbc.TF32X3, zbc.TC2])
+def test_twelve_components_per_column(prec):
+    # q = 12 (a piecewise-linear basis: 4 functions x 3 components per voxel): the product
+    # kernels take q from the handle, four times the work of q = 3
+    rng = np.random.default_rng(31)
+    n = (24, 12, 10)
+    tens = []
+    for _ in range(9):
+        tj = []
+        for _k in range(12):
+            r = tuple(int(rng.integers(1, 9)) for _ in range(3))
+            G = rng.normal(size=r) + 1j * rng.normal(size=r)
+            Us = [np.linalg.qr(rng.normal(size=(ni, ri)) + 1j * rng.normal(size=(ni, ri)))[0] for ni, ri in zip(n, r)]
+            tj.append((G.astype(np.complex64).astype(np.complex128),
+                       [U.astype(np.complex64).astype(np.complex128) for U in Us]))
+        tens.append(tj)
+    grid = inputs.Grid(*n, 0.002)
+    h = zbc.zbc_create_from_host(grid, 12, tens)
+    assert h.info().q == 12
+    p = 5
+    X = inputs.cn01((9, p), seed=7).astype(np.complex64)
+    Y = zbc.colmajor(12 * grid.nv, p, torch.complex64)
+    zbc.zbc_matvec(h, zbc.to_colmajor(X), Y, prec)
+    zbc.zbc_product_status(h)
+    assert rel_cols(zbc.from_colmajor(Y), products.matvec(tens, n, X)).max() < RTOL
+    if prec == zbc.FP32_SIMT:
+        Phi = inputs.cn01((12 * grid.nv, p), seed=8).astype(np.complex64)
+        Psi = zbc.colmajor(9, p, torch.complex64)
+        zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
+        zbc.zbc_product_status(h)
+        assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, n, Phi)).max() < RTOL
+
+
+def test_hosvd_twelve_components():
+    # tucker_compress with q = 12 on planted-rank columns: ranks recovered, error within tol
+    from oracle import tucker as otucker
+    rng = np.random.default_rng(33)
+    n = (16, 12, 10)
+    nv = n[0] * n[1] * n[2]
+    cols, planted = [], []
+    for _ in range(3):
+        col = []
+        for _k in range(12):
+            r = tuple(int(rng.integers(1, 5)) for _ in range(3))
+            G = rng.normal(size=r) + 1j * rng.normal(size=r)
+            Us = [np.linalg.qr(rng.normal(size=(ni, ri)) + 1j * rng.normal(size=(ni, ri)))[0] for ni, ri in zip(n, r)]
+            col.append(otucker.reconstruct(G, Us).reshape(-1, order="F"))
+            # the mode-g rank of a generic core is min(r_g, product of the other two ranks)
+            planted.append(tuple(min(r[gm], r[(gm + 1) % 3] * r[(gm + 2) % 3]) for gm in range(3)))
+        cols.append(np.concatenate(col))
+    Z = np.stack(cols, axis=1)
+    grid = inputs.Grid(*n, 0.002)
+    h, st = zbc.tucker_compress(zbc.to_colmajor(Z.astype(np.complex128)), grid, 1e-10, q=12)
+    ranks, _, _ = h.export()
+    assert [tuple(x) for x in ranks.reshape(-1, 3)] == planted
+    assert st.max_rel_err <= 1e-10 * (1 + 1e-6) + 1e-12
