@@ -189,7 +189,9 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
                         int MJ, StageLayout SL, int S, const float2* __restrict__ Phi, int64_t ldphi, int p,
                         float2* __restrict__ partial, int* __restrict__ err) {
   constexpr int NV = 2 * PS;
-  constexpr int SH = 5 - Log2<NV>::v;
+  constexpr int NH = PS > 8 ? 2 : 1;  // halves of the right-hand sides
+  constexpr int PSH = PS / NH, NVH = 2 * PSH;
+  constexpr int SHH = 5 - Log2<NVH>::v;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
   __shared__ int meta[kMaxStages];
@@ -307,21 +309,28 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
       unsigned char* sb = smem + (size_t)st * SL.stride;
       float2 z[kUQ];
       last_mode_staged((const float2*)(sb + SL.u1), B1p, il, (const float2*)(sb + SL.w), meta[st], u0, z);
-      float vals[NV];
+      // the contraction in halves of at most 8 right-hand sides: two reduce-scatters of 16 values
+      // take as many shuffles as one of 32 and need half the registers
 #pragma unroll
-      for (int i = 0; i < PS; ++i) {
-        float re = 0.f, im = 0.f;
+      for (int hf = 0; hf < NH; ++hf) {
+        float vals[NVH];
 #pragma unroll
-        for (int l = 0; l < kUQ; ++l) {
-          const float2 zz = okl[l] ? z[l] : make_float2(0.f, 0.f);
-          re = fmaf(zz.x, ph[l][i].x, fmaf(zz.y, ph[l][i].y, re));
-          im = fmaf(zz.x, ph[l][i].y, fmaf(-zz.y, ph[l][i].x, im));
+        for (int i = 0; i < PSH; ++i) {
+          float re = 0.f, im = 0.f;
+#pragma unroll
+          for (int l = 0; l < kUQ; ++l) {
+            const float2 zz = okl[l] ? z[l] : make_float2(0.f, 0.f);
+            const float2 f = ph[l][hf * PSH + i];
+            re = fmaf(zz.x, f.x, fmaf(zz.y, f.y, re));
+            im = fmaf(zz.x, f.y, fmaf(-zz.y, f.x, im));
+          }
+          vals[2 * i] = re;
+          vals[2 * i + 1] = im;
         }
-        vals[2 * i] = re;
-        vals[2 * i + 1] = im;
+        const float r = warp_reduce_scatter<NVH>(vals, lane);
+        if ((lane & ((1 << SHH) - 1)) == 0)
+          ((float*)(sb + SL.red))[warp * NV + hf * NVH + (lane >> SHH)] = r;
       }
-      const float r = warp_reduce_scatter<NV>(vals, lane);
-      if ((lane & ((1 << SH) - 1)) == 0) ((float*)(sb + SL.red))[warp * NV + (lane >> SH)] = r;
       __syncwarp();
       if (lane == 0) mbar_arrive1(&empty[st]);
     }
@@ -410,12 +419,7 @@ static int launch_matvec(Handle& h, const float2* X, int64_t ldx, int p, float2*
   const int S = (int)std::min<size_t>(kMaxStages, kSmemBudget / SL.stride);
   ZBC_CHECK_ARG(S >= 2, "rank %d too large for the FP32 SIMT path", R);
   const size_t sm = (size_t)S * SL.stride;
-  static bool attr_set = false;
-  if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_simt_kernel<PS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kSmemBudget));
-    attr_set = true;
-  }
+  ZBC_TRY((set_smem_limit<matvec_simt_kernel<PS, NT>>((int)kSmemBudget)));
   dim3 grid(g.ntiles(), h.q, schunks);
   matvec_simt_kernel<PS, NT><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL, S,
                                                                XT, pst, p, Y, ldy, (int*)h.work_err.ptr);
@@ -456,12 +460,7 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
     scratch = (float2*)h.work_partial.ptr;
   }
   const size_t sm = (size_t)S * SL.stride + sizeof(float) * (size_t)MJ * NV;
-  static bool attr_set = false;
-  if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(rmatvec_simt_kernel<PS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kSmemBudget));
-    attr_set = true;
-  }
+  ZBC_TRY((set_smem_limit<rmatvec_simt_kernel<PS, NT>>((int)kSmemBudget)));
   dim3 grid(G, h.q * jblocks, schunks);
   rmatvec_simt_kernel<PS, NT><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, MJ, SL,
                                                                 S, Phi, ldphi, p, scratch, (int*)h.work_err.ptr);

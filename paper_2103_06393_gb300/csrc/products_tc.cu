@@ -468,12 +468,7 @@ static int launch_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, 
   const float2* XT;
   int pst;
   ZBC_TRY(transpose_rhs(h, X, ldx, p, P, &XT, &pst, st));
-  static bool attr_set = false;
-  if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_tc_kernel<FMT, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)budget));
-    attr_set = true;
-  }
+  ZBC_TRY((set_smem_limit<matvec_tc_kernel<FMT, P2>>((int)budget)));
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
   matvec_tc_kernel<FMT, P2><<<grid, 32 * (L.nprodw + 3), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, SL,
                                                                    S, L, XT, pst, p, Y, ldy, (int*)h.work_err.ptr);

@@ -518,12 +518,7 @@ static int launch_tc2(Handle& h, const float2* X, int64_t ldx, int p, float2* Y,
   const float2* XT;
   int pst;
   ZBC_TRY(transpose_rhs(h, X, ldx, p, P, &XT, &pst, st));
-  static bool attr_set = false;
-  if (!attr_set) {
-    ZBC_TRY_CUDA(cudaFuncSetAttribute(matvec_tc2_kernel<P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      220 * 1024));
-    attr_set = true;
-  }
+  ZBC_TRY((set_smem_limit<matvec_tc2_kernel<P2>>(220 * 1024)));
   dim3 grid(g.ntiles(), h.q, ceil_div(p, P));
   matvec_tc2_kernel<P2><<<grid, kTc2Threads, L.total + 1024, st>>>(h.cache->data, h.cache->d_desc, h.cache->half,
                                                                     h.cache->d_half, g, h.q, h.M, L, XT, pst, p, Y,

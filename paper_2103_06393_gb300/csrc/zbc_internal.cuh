@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -127,6 +129,20 @@ __host__ __device__ __forceinline__ double2 zfma_conj(double2 a, double2 b, doub
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Raise Kernel's dynamic shared-memory limit to `bytes` on the current device, once per device
+// (the attribute is per device; the flags are per kernel and safe across threads).
+template <auto Kernel>
+int set_smem_limit(int bytes) {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  ZBC_TRY_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return ZBC_OK;
+  ZBC_TRY_CUDA(cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_release);
+  return ZBC_OK;
+}
 
 // right-hand-side class of p: 1, 2, 3-4, 5-8, 9-16, 17-32, 33-64, 65+
 inline int rhs_class(int p) {
