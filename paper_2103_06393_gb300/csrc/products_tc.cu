@@ -482,7 +482,13 @@ static int matvec_tc_fmt(Handle& h, const float2* X, int64_t ldx, int p, float2*
   if (p <= 8) return launch_tc<FMT, 16>(h, X, ldx, p, Y, ldy, st);
   if (p <= 16) return launch_tc<FMT, 32>(h, X, ldx, p, Y, ldy, st);
   if (p <= 32) return launch_tc<FMT, 64>(h, X, ldx, p, Y, ldy, st);
-  return launch_tc<FMT, 128>(h, X, ldx, p, Y, ldy, st);
+  // 64 right-hand sides per CTA need D and S of 2 x 128 TMEM columns per 128 voxel rows, which
+  // leaves room for two M tiles only: a tile whose i1 range has three 32-row groups does not
+  // fit, and then the right-hand sides go 32 per CTA instead
+  const int s = launch_tc<FMT, 128>(h, X, ldx, p, Y, ldy, st);
+  if (s != ZBC_EINVAL) return s;
+  clear_error();
+  return launch_tc<FMT, 64>(h, X, ldx, p, Y, ldy, st);
 }
 
 int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, zbc_precision prec,

@@ -192,3 +192,13 @@ def test_hosvd_twelve_components():
     ranks, _, _ = h.export()
     assert [tuple(x) for x in ranks.reshape(-1, 3)] == planted
     assert st.max_rel_err <= 1e-10 * (1 + 1e-6) + 1e-12
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_tc_many_rhs_on_three_group_tiles(prec):
+    # p = 72 on n1 = 96 (three 32-row groups per i1 tile): 64 right-hand sides per CTA do not fit
+    # TMEM with three M tiles, so the forms fall back to 32 per CTA (or fewer u values)
+    w = inputs.scaled_workload("precision", (96, 6, 4), m=12)
+    h, tens = _handle(w, 1e-6)
+    Y, Yo = _fwd(h, w, tens, 72, prec, seed=12)
+    assert rel_cols(Y, Yo).max() < RTOL
