@@ -16,6 +16,8 @@ namespace zbc {
 // NT = compute warps per CTA at most (template): 6 (7 warps with the copy warp, up to 255
 // registers per thread) or 9 (10 warps, 168 registers); chosen per call (zbc_tune), default 9
 constexpr size_t kSmemBudget = 220 * 1024;
+constexpr int kAdjStages = 4;  // adjoint stage ring depth (the per-column sums take the rest; 6 or 8
+                               // measured no faster)
 
 // ---------------------------------------------------------------------------------------------
 // warp reduce-scatter of NV floats per lane: afterwards lane l holds the warp sum of value index
@@ -440,12 +442,13 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   constexpr int NV = 2 * PS;
   const StageLayout SL = StageLayout::make(R, B1p, g.NUp, 0, 4 * NV * g.ntask);
   // stages first (4, or as many as fit), the rest of shared memory holds the j-block's sums
-  const int S = (int)std::min<size_t>(4, kSmemBudget / SL.stride);
+  const int S = (int)std::min<size_t>(kAdjStages, kSmemBudget / SL.stride);
   ZBC_CHECK_ARG(S >= 2, "rank %d too large for the FP32 SIMT adjoint", R);
   const size_t left = kSmemBudget - (size_t)S * SL.stride;
-  const int MJ = (int)std::min<size_t>(h.M, left / (sizeof(float) * NV));
-  ZBC_CHECK_ARG(MJ >= 1, "rank %d too large for the FP32 SIMT adjoint", R);
-  const int jblocks = ceil_div(h.M, MJ);
+  const int MJmax = (int)std::min<size_t>(h.M, left / (sizeof(float) * NV));
+  ZBC_CHECK_ARG(MJmax >= 1, "rank %d too large for the FP32 SIMT adjoint", R);
+  const int jblocks = ceil_div(h.M, MJmax);
+  const int MJ = ceil_div(h.M, jblocks);  // balanced j-blocks
   const int schunks = ceil_div(p, PS);
   const size_t per_group = sizeof(float2) * (size_t)h.q * h.M * p;
   int G = std::max(1, sm_count() / std::max(1, h.q * jblocks * schunks));
