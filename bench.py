@@ -624,7 +624,7 @@ def run_reference(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": "precision: 96^3 voxels (2 mm), 8-loop coil, 1024 segments, 298.2 MHz, "
-                               "HOSVD tol 1e-6, p=16", "path": "FP64 CPU oracle"},
+                               "HOSVD tol 1e-6, complex128 Tucker storage, p=16", "path": "FP64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{ncols} of {s.m} columns per step, scaled linearly"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

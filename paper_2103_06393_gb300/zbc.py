@@ -133,6 +133,8 @@ def _ld(t) -> int:
     column may carry any stride for its size-1 dimension, so its ld is its row count."""
     if t.shape[0] == 1:
         return int(t.shape[1])
+    if t.shape[1] == 1:  # one row: the within-column stride is irrelevant
+        return max(1, int(t.stride(0)))
     assert t.stride(1) == 1, "column-major buffers need unit stride within a column"
     return int(t.stride(0))
 

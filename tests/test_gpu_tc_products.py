@@ -202,3 +202,21 @@ def test_tc_many_rhs_on_three_group_tiles(prec):
     h, tens = _handle(w, 1e-6)
     Y, Yo = _fwd(h, w, tens, 72, prec, seed=12)
     assert rel_cols(Y, Yo).max() < RTOL
+
+
+@pytest.mark.parametrize("prec", [zbc.FP32_SIMT] + TC)
+@pytest.mark.parametrize("M", [1, 3, 9])
+def test_few_columns(prec, M):
+    # fewer columns than a chunk, a stage ring, or one producer half's share
+    w = inputs.scaled_workload("precision", (20, 14, 6), m=M)
+    h, tens = _handle(w, 1e-6)
+    for p in (1, 3):
+        Y, Yo = _fwd(h, w, tens, p, prec, seed=M + p)
+        assert rel_cols(Y, Yo).max() < RTOL
+    if prec == zbc.FP32_SIMT:
+        g = w.grid
+        Phi = inputs.cn01((3 * g.nv, 2), seed=M).astype(np.complex64)
+        Psi = zbc.colmajor(M, 2, torch.complex64)
+        zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
+        zbc.zbc_product_status(h)
+        assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, g.shape, Phi)).max() < RTOL
