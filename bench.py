@@ -199,6 +199,19 @@ def time_steps(fn, steps, flush, torch, stream):
     return times
 
 
+def mode1_gemm_flops(h, w, p):
+    """Real tensor-core flops of the mode-1 adjoint's GEMMs: per group of 128 (column, rank) rows
+    of one component, M = 128, K = 2 n1 (Re, Im of each i1), N = 2 n2 n3 P per pass of P <= 16
+    right-hand sides, times 3 fp16 products (hi.hi, hi.lo, lo.hi)."""
+    g = w.grid
+    ranks = h.export()[0]                      # (M, q, 3)
+    groups = sum(-(-int(ranks[:, k, 0].sum()) // 128) for k in range(ranks.shape[1]))
+    P = 1 << max(0, (min(p, 16) - 1).bit_length())
+    nsc = -(-p // P)
+    n1p = -(-g.shape[0] // 8) * 8
+    return 2.0 * 128 * (2 * n1p) * (2 * g.shape[1] * g.shape[2] * P * nsc) * 3 * groups
+
+
 def run_zbc(args):
     import torch
 
@@ -233,11 +246,12 @@ def run_zbc(args):
     def flush():
         flushbuf.fill_(1)
 
-    names = {zbc.FP32_SIMT: "fp32_simt", zbc.TF32X3: "tf32x3", zbc.BF16X3: "bf16x3", zbc.TC2: "tc2"}
+    names = {zbc.FP32_SIMT: "fp32_simt", zbc.TF32X3: "tf32x3", zbc.BF16X3: "bf16x3", zbc.TC2: "tc2",
+             zbc.TC_MODE1: "tc_mode1"}
 
-    def available(fn, a, b):
+    def available(fn, a, b, codes):
         out = [zbc.FP32_SIMT]
-        for code in (zbc.TF32X3, zbc.BF16X3, zbc.TC2):
+        for code in codes:
             try:
                 fn(h, a, b, code)
                 out.append(code)
@@ -245,8 +259,8 @@ def run_zbc(args):
                 pass
         return [c for c in out if args.prec in ("auto", names[c])] or [zbc.FP32_SIMT]
 
-    fwd_codes = available(zbc.zbc_matvec, Xd, Yd)
-    adj_codes = available(zbc.zbc_rmatvec, Phid, Psid)
+    fwd_codes = available(zbc.zbc_matvec, Xd, Yd, (zbc.TF32X3, zbc.BF16X3, zbc.TC2))
+    adj_codes = available(zbc.zbc_rmatvec, Phid, Psid, (zbc.TC_MODE1,))
     tens, _ = h.tensors()
     nt = max(3, args.steps // 2)
     # every form's output is kept for the oracle check (rank 0, with the CPU baseline); all of
@@ -276,13 +290,13 @@ def run_zbc(args):
         fv = min((k for k in tune if k.startswith("fwd_")), key=lambda k: tune[k])
         av = min((k for k in tune if k.startswith("adj_")), key=lambda k: tune[k])
         fwd_head = "fp32_simt" if "simt" in fv else fv[4:]
-        adj_head = "fp32_simt"
+        adj_head = "fp32_simt" if "simt" in av else "tc_" + av[4:]
         fcode = acode = zbc.AUTO
         variant = {"forward": fv, "adjoint": av}
     else:
         fwd_head = min(fwd, key=lambda n: fwd[n]["ms"])
-        adj_head = "fp32_simt"
-        fcode, acode = fwd[fwd_head]["code"], zbc.FP32_SIMT
+        adj_head = min(adj, key=lambda n: adj[n]["ms"])
+        fcode, acode = fwd[fwd_head]["code"], adj[adj_head]["code"]
         variant = {"forward": fwd_head, "adjoint": adj_head}
     for _ in range(args.warmup):
         zbc.zbc_matvec(h, Xd, Yd, fcode)
@@ -344,7 +358,8 @@ def run_zbc(args):
     # the dominant kernel: the slower of the two products' main kernels
     dom_fwd = fwd_ms >= adj_ms
     dom_name, dom_ms = (fwd_head, fwd_ms) if dom_fwd else (adj_head, adj_ms)
-    kern = ("matvec" if dom_fwd else "rmatvec") + ("_simt_kernel" if dom_name == "fp32_simt" else "_tc_kernel")
+    kern = ("matvec" if dom_fwd else "rmatvec") + {"fp32_simt": "_simt_kernel", "tc_mode1": "_mode1_kernel",
+                                                   "tc2": "_tc2_kernel"}.get(dom_name, "_tc_kernel")
     if dom_name == "fp32_simt":
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         mx = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -353,12 +368,20 @@ def run_zbc(args):
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {mx:.0f} MHz",
                 "kernel": kern, "traffic": None}
     else:
-        mult = 6.0
+        # real tensor-core products per real MAC of the split: BF16x3 6, TF32x3 3 at half the bf16
+        # rate (= 6), fp16 hi/lo (TC_MODE1) 3
+        mult = 3.0 if dom_name == "tc_mode1" else 6.0
         bf = peaks.get("bf16_tflops", 1900.0)
         peak = bf / mult
         roof = {"bound": "tensor", "achieved": F1 / (dom_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"measured bf16 {bf} TFLOP/s / 6 real products per complex-split MAC",
+                "peak_source": f"measured bf16 {bf} TFLOP/s / {mult:.0f} real products per split MAC",
                 "kernel": kern, "traffic": None}
+        if dom_name == "tc_mode1":
+            # the mode-1 form's own GEMM (T = U1^H Phi per group of 128 rows, 3 fp16 products)
+            gf = mode1_gemm_flops(h, w, p)
+            roof["gemm"] = {"tflops": gf / (dom_ms * 1e-3) / 1e12, "peak": bf,
+                            "frac": gf / (dom_ms * 1e-3) / 1e12 / bf,
+                            "counts": "2 x 128 rows x 2 n1 x 2 (n2 n3 p) x 3 products per group"}
     # DRAM bytes per launch of the dominant kernel on this workload, from a one-pass ncu capture
     # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; only for the full workload
     # and the kernel version it was taken on

@@ -60,11 +60,23 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  * TC2       : (forward only) the last mode product of the decompression on the tensor cores
  *             too: Z = U1 W per column as a tcgen05 MMA with fp16 hi+lo operands (W scaled by a
  *             power of two per tensor), chained through TMEM into the BF16X3 contraction.
+ * TC_MODE1  : (adjoint only) Psi = Z^H Phi regrouped so that the mode-1 product is one dense
+ *             tcgen05 GEMM per group of 128 (column, rank) rows: T = U1^H Phi^k on the tensor
+ *             cores (fp16 hi+lo operands, scaled by powers of two, 3 products, FP32
+ *             accumulation), then Psi_j = sum conj(W) T over (rank, i2, i3) on CUDA cores.
+ *             Needs n1 <= 224.
  * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
  *             right-hand-side class; before any tuning, BF16X3 for the forward product when
  *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,
  *             but their last bits differ, so AUTO results depend on the tuning. */
-typedef enum { ZBC_FP32_SIMT = 0, ZBC_TF32X3 = 1, ZBC_BF16X3 = 2, ZBC_AUTO = 3, ZBC_TC2 = 4 } zbc_precision;
+typedef enum {
+  ZBC_FP32_SIMT = 0,
+  ZBC_TF32X3 = 1,
+  ZBC_BF16X3 = 2,
+  ZBC_AUTO = 3,
+  ZBC_TC2 = 4,
+  ZBC_TC_MODE1 = 5
+} zbc_precision;
 
 typedef enum { ZBC_HOSVD = 0, ZBC_RANDOMIZED_LEARNED = 1, ZBC_RANDOMIZED_FIXED = 2 } zbc_tucker_method;
 
@@ -250,7 +262,9 @@ int zbc_matvec(const zbc_handle* h, const void* X, int64_t ldx, int p, void* Y, 
  *   Phi : device complex64, (q*n_v) x p, ldphi >= q*n_v
  *   Psi : device complex64, m x p, ldpsi >= m; overwritten
  * Partial sums over voxel tiles are reduced in a fixed order (deterministic).
- * prec: ZBC_FP32_SIMT or ZBC_AUTO; the adjoint has no tensor-core form (ZBC_EINVAL).
+ * prec: ZBC_FP32_SIMT, ZBC_TC_MODE1 or ZBC_AUTO (others: ZBC_EINVAL).  TC_MODE1 keeps fp16
+ * copies of Phi (16 bytes per complex entry, rounded up to whole N blocks) and partial sums in
+ * per-handle workspaces.
  */
 int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void* Psi,
                 int64_t ldpsi, zbc_precision prec, zbc_stream stream);
@@ -279,10 +293,10 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
  * zbc_tune -- autotuner of the product kernels (no counterpart in the paper).  Times, on this
  * handle with p right-hand sides (zero-filled scratch operands), every variant of
  *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2
- *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA
+ *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA, TC_MODE1
  * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
- * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the adjoint's choice).
- *   times_ms_host : optional float[7], the variants' times in the order above (ms per call;
+ * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the faster SIMT shape).
+ *   times_ms_host : optional float[8], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
  */
@@ -331,7 +345,8 @@ int zbc_export_host(const zbc_handle* h, int32_t* ranks_host, void* pool_host, v
  * zbc_tc_selftest -- diagnostic of the tensor-core operand path (no counterpart in the paper):
  * D (128 x N, row-major) = A (128 x K, row-major) * B (N x K, row-major)^T computed with one
  * chain of tcgen05.mma through the shared-memory layout and descriptors of the product
- * kernels, operands rounded to fmt (0 = fp16, 1 = bf16, 2 = tf32), FP32 accumulation.
+ * kernels, operands rounded to fmt (0 = fp16, 1 = bf16, 2 = tf32), FP32 accumulation;
+ * fmt 3 / 4 are fp16 / bf16 with A read from tensor memory (the mode-1 adjoint's form).
  * Host pointers; N in {16, 32, 48, 64}; K a multiple of 16 (fp16/bf16) or 8 (tf32), <= 64.
  * Synchronises the device.  Returns ZBC_ETIMEOUT if the MMA completion wait gave up.
  */

@@ -104,13 +104,18 @@ struct HalfDesc {
   int uexp;     // |U1| < 2^uexp (set on the device by the cache build)
 };
 
+struct Mode1Cache;  // operands of the mode-1 adjoint (products_mode1.cu), built on its first use
+void mode1_release(Mode1Cache* c);
+
 struct DecompCache {
   float2* data = nullptr;   // W blocks and tile-blocked U1
   CacheDesc* d_desc = nullptr;
+  std::vector<CacheDesc> host_desc;
   int64_t elems = 0;
   unsigned char* half = nullptr;  // fp16 U1 operand blocks (built on first use of the chained path)
   HalfDesc* d_half = nullptr;
   int kb1_max = 0;
+  Mode1Cache* mode1 = nullptr;
 };
 int build_decomp_cache(Handle& h, cudaStream_t st);
 int build_half_cache(Handle& h, cudaStream_t st);

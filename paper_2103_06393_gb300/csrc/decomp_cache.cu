@@ -20,6 +20,7 @@ void cache_release(DecompCache* c) {
   if (c->d_desc) cudaFree(c->d_desc);
   if (c->half) cudaFree(c->half);
   if (c->d_half) cudaFree(c->d_half);
+  mode1_release(c->mode1);
   delete c;
 }
 
@@ -95,6 +96,7 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
   ZBC_TRY_CUDA(cudaMemsetAsync(h.work_err.ptr, 0, sizeof(int), st));
   auto* c = new DecompCache();
   c->elems = off;
+  c->host_desc = cd;
   cudaError_t e = cudaMalloc(&c->data, sizeof(float2) * std::max<int64_t>(1, off));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_desc, sizeof(CacheDesc) * T);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_desc, cd.data(), sizeof(CacheDesc) * T, cudaMemcpyHostToDevice, st);

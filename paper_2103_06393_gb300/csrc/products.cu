@@ -27,8 +27,9 @@ static int matvec_impl(Handle& h, const float2* X, int64_t ldx, int p, float2* Y
   return matvec_tc(h, Xe, ldxe, p, Y, ldy, prec, st);
 }
 
-static int rmatvec_impl(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* Psi, int64_t ldpsi, int warps,
-                        cudaStream_t st) {
+// Psi = Z^H Phi with an explicit form: FP32_SIMT (with `warps` compute warps) or TC_MODE1
+static int rmatvec_impl(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* Psi, int64_t ldpsi,
+                        zbc_precision prec, int warps, cudaStream_t st) {
   float2* out = Psi;
   int64_t ldo = ldpsi;
   if (h.has_v) {
@@ -36,7 +37,10 @@ static int rmatvec_impl(Handle& h, const float2* Phi, int64_t ldphi, int p, floa
     out = (float2*)h.work_x.ptr;
     ldo = h.M;
   }
-  ZBC_TRY(rmatvec_simt(h, Phi, ldphi, p, out, ldo, warps, st));
+  if (prec == ZBC_TC_MODE1)
+    ZBC_TRY(rmatvec_mode1(h, Phi, ldphi, p, out, ldo, st));
+  else
+    ZBC_TRY(rmatvec_simt(h, Phi, ldphi, p, out, ldo, warps, st));
   if (h.has_v) return aca_post(h, out, p, Psi, ldpsi, st);
   return ZBC_OK;
 }
@@ -53,8 +57,9 @@ extern "C" int zbc_matvec(const zbc_handle* hh, const void* X, int64_t ldx, int 
   ZBC_CHECK_ARG(ldx >= h.m, "ldx (%lld) < m (%d)", (long long)ldx, h.m);
   ZBC_CHECK_ARG(ldy >= (int64_t)h.q * h.nv(), "ldy < q*n_v");
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
-                    prec == ZBC_TC2,
+                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1,
                 "unknown precision %d", (int)prec);
+  ZBC_CHECK_ARG(prec != ZBC_TC_MODE1, "ZBC_TC_MODE1 is a form of the adjoint product only");
   const int cls = rhs_class(p);
   int warps = h.tune_fwd_warps[cls];
   if (prec == ZBC_AUTO)
@@ -71,11 +76,13 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   ZBC_CHECK_ARG(ldphi >= (int64_t)h.q * h.nv(), "ldphi < q*n_v");
   ZBC_CHECK_ARG(ldpsi >= h.m, "ldpsi (%lld) < m (%d)", (long long)ldpsi, h.m);
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
-                    prec == ZBC_TC2,
+                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1,
                 "unknown precision %d", (int)prec);
-  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_AUTO,
-                "the adjoint product has no tensor-core form: use ZBC_FP32_SIMT or ZBC_AUTO");
-  return rmatvec_impl(h, (const float2*)Phi, ldphi, p, (float2*)Psi, ldpsi, h.tune_adj_warps[rhs_class(p)],
+  ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_AUTO || prec == ZBC_TC_MODE1,
+                "the adjoint product's forms are ZBC_FP32_SIMT, ZBC_TC_MODE1 and ZBC_AUTO");
+  const int cls = rhs_class(p);
+  if (prec == ZBC_AUTO) prec = h.tune_adj_prec[cls] >= 0 ? (zbc_precision)h.tune_adj_prec[cls] : ZBC_FP32_SIMT;
+  return rmatvec_impl(h, (const float2*)Phi, ldphi, p, (float2*)Psi, ldpsi, prec, h.tune_adj_warps[cls],
                       (cudaStream_t)stream);
 }
 
@@ -101,17 +108,17 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
     zbc_precision prec;
     int warps;
   };
-  constexpr int NV = 7;
-  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6}, {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
-                            {true, ZBC_BF16X3, 0},    {true, ZBC_TC2, 0},         {false, ZBC_FP32_SIMT, 6},
-                            {false, ZBC_FP32_SIMT, 9}};
+  constexpr int NV = 8;
+  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6},  {true, ZBC_FP32_SIMT, 9},  {true, ZBC_TF32X3, 0},
+                            {true, ZBC_BF16X3, 0},     {true, ZBC_TC2, 0},        {false, ZBC_FP32_SIMT, 6},
+                            {false, ZBC_FP32_SIMT, 9}, {false, ZBC_TC_MODE1, 0}};
   float t[NV];
   int status = ZBC_OK;
   for (int i = 0; i < NV && status == ZBC_OK; ++i) {
     const Variant& v = vars[i];
     auto run = [&]() {
       return v.fwd ? matvec_impl(h, (const float2*)X.ptr, h.m, p, (float2*)Y.ptr, rows, v.prec, v.warps, st)
-                   : rmatvec_impl(h, (const float2*)Phi.ptr, rows, p, (float2*)Psi.ptr, h.m, v.warps, st);
+                   : rmatvec_impl(h, (const float2*)Phi.ptr, rows, p, (float2*)Psi.ptr, h.m, v.prec, v.warps, st);
     };
     t[i] = INFINITY;
     if (run() != ZBC_OK) {  // a form that does not fit this handle is skipped
@@ -138,7 +145,7 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   cudaEventDestroy(e1);
   if (status != ZBC_OK) return status;
   if (!(t[0] < INFINITY || t[1] < INFINITY || t[2] < INFINITY || t[3] < INFINITY || t[4] < INFINITY) ||
-      !(t[5] < INFINITY || t[6] < INFINITY)) {
+      !(t[5] < INFINITY || t[6] < INFINITY || t[7] < INFINITY)) {
     set_error("zbc_tune: no product form fits this handle");
     return ZBC_EINVAL;
   }
@@ -146,10 +153,13 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   int bf = 0, ba = 5;
   for (int i = 1; i < 5; ++i)
     if (t[i] < t[bf]) bf = i;
-  if (t[6] < t[5]) ba = 6;
+  for (int i = 6; i < NV; ++i)
+    if (t[i] < t[ba]) ba = i;
   h.tune_fwd_prec[cls] = (int8_t)vars[bf].prec;
   h.tune_fwd_warps[cls] = (int8_t)vars[bf].warps;
-  h.tune_adj_warps[cls] = (int8_t)vars[ba].warps;
+  h.tune_adj_prec[cls] = (int8_t)vars[ba].prec;
+  // the SIMT CTA shape stays the faster of the two SIMT variants (zbc_rmatvec_noalloc uses it)
+  h.tune_adj_warps[cls] = (int8_t)(t[6] < t[5] ? 9 : 6);
   if (times_ms_host)
     for (int i = 0; i < NV; ++i) times_ms_host[i] = t[i];
   return ZBC_OK;

@@ -1,0 +1,610 @@
+// Adjoint product (Algorithm 2, Sec. III.B) with the mode-1 product on the tensor cores.
+//
+// With Z^{kj}[i1, i23] = sum_a U1_{kj}[i1, a] W_{kj}[i23, a]  (i23 = i2 + n2 i3, W = G x2 U2 x3 U3,
+// the decompression cache of decomp_cache.cu), the adjoint regroups as
+//   Psi_j[s] = sum_k sum_a sum_i23 conj(W_{kj}[i23, a]) T_{kja}[i23, s],
+//   T_{kja}[i23, s] = sum_i1 conj(U1_{kj}[i1, a]) Phi^k[i1 + n1 i23, s],
+// i.e. Phi^k is first projected onto the mode-1 factors.  Stacking the (column j, rank a) pairs
+// of component k as rows, 128 to a group, the projection is one dense GEMM per group,
+//   T[(j, a)][(i23, s)] = U1^H [128 x n1] . Phi^k [n1 x (n2 n3 p)],
+// which runs on tcgen05; the remaining sum over (a, i23) is a short epilogue on CUDA cores that
+// reads T from tensor memory.  Per (row, i23, s) it costs one complex multiply-add, against
+// r1 + p of the decompress-then-contract form (products_simt.cu), and the GEMM carries the
+// rest: the tensor cores do ~r1 times the flops of Table III's count, at ~25 times the FP32 rate.
+//
+// Real embedding (K = 2 i1 + e', both operands K-major):
+//   A[(j, a)][2 i1 + e'] = (Re, Im) U1[i1, a]                     (tensor memory, per group)
+//   B[2 (i23l P + s) + 0][2 i1 + e'] = (Re, Im) Phi[i1, i23, s]   -> D = Re T
+//   B[2 (i23l P + s) + 1][2 i1 + e'] = (Im, -Re) Phi[i1, i23, s]  -> D = Im T
+// Precision: both operands are split into fp16 hi + lo (x = hi + lo to ~2^-22 relative), after
+// scaling by powers of two into fp16's normal range -- per row of A (2^(kHalfShift - uexp)) and
+// per N block of B (2^(kHalfShift - e_blk)) -- and the three products hi.hi + hi.lo + lo.hi
+// accumulate in FP32; the scales are removed exactly in the epilogue.
+//
+// Kernels, per call:
+//   phi_split_kernel      Phi -> the B operand blocks (fp16 hi / lo, one contiguous run per
+//                         (component, RHS chunk, N block, K chunk)) and one exponent per N block
+//   rmatvec_mode1_kernel  persistent, one CTA per SM; items (RHS chunk, N range, group):
+//                         4 epilogue warps (A into TMEM, T . conj(W) sums), a copy warp
+//                         (cp.async.bulk of the B blocks into a stage ring) and an MMA warp
+//                         (A from TMEM, B from shared memory, D double-buffered in TMEM)
+//   mode1_reduce_kernel   Psi'[j, s] = sum over N ranges, components and ranks, fixed order
+// plus, once per handle, mode1_build_kernel (the A operand and the row table).
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "stage.cuh"
+
+namespace zbc {
+
+constexpr int kM1Rows = 128;       // (column, rank) rows per group = MMA M = TMEM lanes
+constexpr int kM1MaxP = 16;        // right-hand sides per pass
+constexpr int kM1MaxStages = 8;
+constexpr int kM1Threads = 32 * 6;  // 4 epilogue warps, the copy warp, the MMA warp
+constexpr int kM1MaxN1p = 224;     // A (2 n1p TMEM columns) + two D buffers of >= 32 columns
+
+struct Mode1Row {
+  int64_t wbase;  // W_{kj}[i23 = 0, a] in the decompression cache; -1 for a padding row
+  int r1p;        // W's stride per i23
+  int uexp;       // max |Re|, |Im| of U1_{kj}[:, a] < 2^uexp (set by the build kernel)
+};
+
+struct Mode1Cache {
+  int KG = 0;                 // groups over all components
+  int n1p = 0;                // n1 rounded up to 8 (K = 2 n1p reals)
+  uint32_t* A = nullptr;      // [KG][2 terms][n1p / 4][128 rows][4] fp16x2 (Re low, Im high)
+  Mode1Row* rows = nullptr;   // [KG * 128]
+  int* kg_k = nullptr;        // [KG] component of each group
+  int2* colrows = nullptr;    // [M q], tensor t = j q + k -> (first global row, r1)
+  int4* rowsrc = nullptr;     // [KG * 128] (tensor, a, valid) for the build
+};
+
+void mode1_release(Mode1Cache* c) {
+  if (!c) return;
+  if (c->A) cudaFree(c->A);
+  if (c->rows) cudaFree(c->rows);
+  if (c->kg_k) cudaFree(c->kg_k);
+  if (c->colrows) cudaFree(c->colrows);
+  if (c->rowsrc) cudaFree(c->rowsrc);
+  delete c;
+}
+
+// One thread per row (j, a): exponent of U1[:, a], then the scaled fp16 hi / lo split.
+__global__ void __launch_bounds__(128) mode1_build_kernel(const float2* __restrict__ pool,
+                                                          const TensorDesc* __restrict__ desc,
+                                                          const int4* __restrict__ rowsrc, int n1, int n1p,
+                                                          uint32_t* __restrict__ A, Mode1Row* __restrict__ rows) {
+  const int kg = blockIdx.x, l = threadIdx.x;
+  const int4 src = rowsrc[(int64_t)kg * kM1Rows + l];
+  const float2* U1 = nullptr;
+  float mx = 0.f;
+  if (src.z) {
+    const TensorDesc d = desc[src.x];
+    U1 = pool + d.off + (int64_t)d.r1 * d.r2 * d.r3 + (int64_t)n1 * src.y;
+    for (int i1 = 0; i1 < n1; ++i1) {
+      const float2 u = U1[i1];
+      mx = fmaxf(mx, fmaxf(fabsf(u.x), fabsf(u.y)));
+    }
+  }
+  int uexp = 0;
+  frexpf(mx, &uexp);  // mx < 2^uexp (mx = 0 gives 0)
+  if (src.z) rows[(int64_t)kg * kM1Rows + l].uexp = uexp;
+  const int sh = kHalfShift - uexp;
+  for (int i1 = 0; i1 < n1p; ++i1) {
+    const float2 u = (U1 && i1 < n1) ? U1[i1] : make_float2(0.f, 0.f);
+    const float xr = ldexpf(u.x, sh), xi = ldexpf(u.y, sh);
+    const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+    const __half lr = __float2half_rn(xr - __half2float(hr)), li = __float2half_rn(xi - __half2float(hi));
+    const __half2 vh = __halves2half2(hr, hi), vl = __halves2half2(lr, li);
+    const int64_t base = ((int64_t)kg * 2 * (n1p / 4) + i1 / 4) * (kM1Rows * 4) + l * 4 + (i1 & 3);
+    A[base] = *reinterpret_cast<const uint32_t*>(&vh);
+    A[base + (int64_t)(n1p / 4) * (kM1Rows * 4)] = *reinterpret_cast<const uint32_t*>(&vl);
+  }
+}
+
+int build_mode1_cache(Handle& h, cudaStream_t st) {
+  ZBC_TRY(build_decomp_cache(h, st));
+  DecompCache& dc = *h.cache;
+  if (dc.mode1) return ZBC_OK;
+  const int q = h.q, M = h.M;
+  std::vector<int> gbase(q + 1, 0);
+  std::vector<int64_t> rstart(q, 0);
+  for (int k = 0; k < q; ++k) {
+    int64_t R = 0;
+    for (int j = 0; j < M; ++j) R += h.desc[(size_t)j * q + k].r1;
+    gbase[k + 1] = gbase[k] + (int)((R + kM1Rows - 1) / kM1Rows);
+  }
+  const int KG = gbase[q];
+  if (KG == 0) {
+    set_error("mode-1 adjoint: the handle has no rows");
+    return ZBC_EINVAL;
+  }
+  std::vector<Mode1Row> rows((size_t)KG * kM1Rows, Mode1Row{-1, 0, 0});
+  std::vector<int4> src((size_t)KG * kM1Rows, make_int4(0, 0, 0, 0));
+  std::vector<int> kg_k(KG);
+  std::vector<int2> colrows((size_t)M * q);
+  for (int k = 0; k < q; ++k) {
+    for (int g = gbase[k]; g < gbase[k + 1]; ++g) kg_k[g] = k;
+    int64_t r = (int64_t)gbase[k] * kM1Rows;
+    for (int j = 0; j < M; ++j) {
+      const int t = j * q + k;
+      const CacheDesc& cd = dc.host_desc[t];
+      colrows[t] = make_int2((int)r, cd.r1);
+      for (int a = 0; a < cd.r1; ++a, ++r) {
+        rows[r] = Mode1Row{cd.woff + a, cd.r1p, 0};
+        src[r] = make_int4(t, a, 1, 0);
+      }
+    }
+  }
+  auto* c = new Mode1Cache();
+  c->KG = KG;
+  c->n1p = (h.n1 + 7) / 8 * 8;
+  const size_t abytes = sizeof(uint32_t) * (size_t)KG * 2 * c->n1p * kM1Rows;
+  cudaError_t e = cudaMalloc(&c->A, abytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->rows, sizeof(Mode1Row) * rows.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->kg_k, sizeof(int) * KG);
+  if (e == cudaSuccess) e = cudaMalloc(&c->colrows, sizeof(int2) * colrows.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->rowsrc, sizeof(int4) * src.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->rows, rows.data(), sizeof(Mode1Row) * rows.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->kg_k, kg_k.data(), sizeof(int) * KG, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->colrows, colrows.data(), sizeof(int2) * colrows.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->rowsrc, src.data(), sizeof(int4) * src.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    mode1_build_kernel<<<KG, kM1Rows, 0, st>>>(h.d_pool, h.d_desc, c->rowsrc, h.n1, c->n1p, c->A, c->rows);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+  if (e != cudaSuccess) {
+    mode1_release(c);
+    set_error("mode-1 adjoint cache build failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
+  }
+  dc.mode1 = c;
+  return ZBC_OK;
+}
+
+// B operand geometry of one call: N blocks of NB rows (I = NB / (2P) values of i23, each with P
+// right-hand sides times (Re, Im) rows), K in nkc chunks of KC i1 (the last may be shorter).
+struct M1Geo {
+  int P, NB, I;       // RHS per pass, rows per N block, i23 per N block
+  int nsc;            // passes over the right-hand sides (ceil(p / P))
+  int n23, NBT;       // n2 n3, N blocks per (component, pass)
+  int n1, n1p, KC, nkc;
+  uint32_t chunk_u32;  // one term of one K chunk: NB * KC 32-bit words
+  __host__ __device__ int64_t block_u32(int k, int sc, int nb, int c) const {
+    return ((((int64_t)k * nsc + sc) * NBT + nb) * nkc + c) * 2 * chunk_u32;
+  }
+};
+
+// One CTA per (N block, pass, component): the block's largest |Re|, |Im| fixes its exponent,
+// then each thread writes 16-byte pieces (4 i1 of one row, both terms) in the canonical K-major
+// layout of tc_common.cuh (rows grouped by 8, KC / 4 pieces per row per chunk).
+__global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict__ Phi, int64_t ldphi, int p,
+                                                        int64_t nv, M1Geo G, uint32_t* __restrict__ Bop,
+                                                        int* __restrict__ Eblk) {
+  const int nb = blockIdx.x, sc = blockIdx.y, k = blockIdx.z;
+  const int KB4 = G.KC / 4;
+  const int npiece = G.NB * G.nkc * KB4;
+  __shared__ float wmax[8];
+  __shared__ int sexp;
+  // piece index -> (chunk c, row n, piece kc within the row's chunk), ordered by output address
+  auto decode = [&](int pi, int& c, int& n, int& kc) {
+    const int r8 = pi & 7;
+    const int rest = pi >> 3;
+    kc = rest % KB4;
+    const int ng = (rest / KB4) % (G.NB / 8);
+    c = rest / (KB4 * (G.NB / 8));
+    n = ng * 8 + r8;
+  };
+  auto source = [&](int n, int c, int kc, int& i1, int64_t& off) {  // false: a padding piece
+    const int i23 = nb * G.I + n / (2 * G.P);
+    const int s = sc * G.P + (n >> 1) % G.P;
+    i1 = c * G.KC + kc * 4;
+    off = (int64_t)k * nv + (int64_t)G.n1 * i23 + ldphi * s;
+    return i23 < G.n23 && s < p;
+  };
+  float mx = 0.f;
+  for (int pi = threadIdx.x; pi < npiece; pi += blockDim.x) {
+    int c, n, kc, i1;
+    int64_t off;
+    decode(pi, c, n, kc);
+    if ((n & 1) || !source(n, c, kc, i1, off)) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i1 + i < G.n1) {
+        const float2 v = Phi[off + i1 + i];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    int e = 0;
+    frexpf(m, &e);
+    sexp = e;
+    Eblk[((int64_t)k * G.nsc + sc) * G.NBT + nb] = e;
+  }
+  __syncthreads();
+  const int sh = kHalfShift - sexp;
+  uint32_t* out = Bop + G.block_u32(k, sc, nb, 0);
+  for (int pi = threadIdx.x; pi < npiece; pi += blockDim.x) {
+    int c, n, kc, i1;
+    int64_t off;
+    decode(pi, c, n, kc);
+    uint32_t hw[4], lw[4];
+    const bool ok = source(n, c, kc, i1, off);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 v = (ok && i1 + i < G.n1) ? Phi[off + i1 + i] : make_float2(0.f, 0.f);
+      if (n & 1) v = make_float2(v.y, -v.x);  // the Im T row
+      const float xr = ldexpf(v.x, sh), xi = ldexpf(v.y, sh);
+      const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+      const __half lr = __float2half_rn(xr - __half2float(hr)), li = __float2half_rn(xi - __half2float(hi));
+      const __half2 vh = __halves2half2(hr, hi), vl = __halves2half2(lr, li);
+      hw[i] = *reinterpret_cast<const uint32_t*>(&vh);
+      lw[i] = *reinterpret_cast<const uint32_t*>(&vl);
+    }
+    // chunk c, term t: (c * 2 + t) * chunk_u32; piece (n, kc) at core_off(n, kc, KB4) bytes
+    const int64_t o = (int64_t)c * 2 * G.chunk_u32 + tc::core_off(n, kc, KB4) / 4;
+    *reinterpret_cast<uint4*>(out + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(out + o + G.chunk_u32) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+struct M1Params {
+  const uint32_t* A;
+  const Mode1Row* rows;
+  const int* kg_k;
+  const float2* W;  // decompression cache
+  const uint32_t* Bop;
+  const int* Eblk;
+  float2* partial;  // [NR][KG * 128][ppad]
+  int* err;
+  M1Geo G;
+  int KG, NR, S, ppad;
+  uint32_t tcols;   // allocated TMEM columns
+  int64_t nitems;   // nsc * NR * KG
+};
+
+// item -> (pass sc, N range nr, group kg); groups vary fastest, so the CTAs running at one time
+// share their N range and read the same B blocks (from L2)
+__device__ __forceinline__ void m1_item(const M1Params& prm, int64_t it, int& sc, int& nr, int& kg, int& nb0,
+                                        int& nb1) {
+  kg = (int)(it % prm.KG);
+  const int64_t t = it / prm.KG;
+  nr = (int)(t % prm.NR);
+  sc = (int)(t / prm.NR);
+  nb0 = (int)((int64_t)prm.G.NBT * nr / prm.NR);
+  nb1 = (int)((int64_t)prm.G.NBT * (nr + 1) / prm.NR);
+}
+
+template <int P, int NB>
+__global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Params prm) {
+  constexpr int I = NB / (2 * P);  // i23 per N block
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t sfull[kM1MaxStages], sempty[kM1MaxStages], dfull[2], dempty[2], afull;
+  __shared__ uint32_t tbase;
+  __shared__ volatile int abort_flag;
+  unsigned char* stages = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const M1Geo& G = prm.G;
+  const int S = prm.S;
+  const uint32_t stage_bytes = 8u * G.chunk_u32;  // both terms of one K chunk
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (warp == 0) tc::tmem_alloc(&tbase, prm.tcols);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&sfull[s], 1);
+      tc::mbar_init(&sempty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&dfull[b], 1);
+      tc::mbar_init(&dempty[b], 4);
+    }
+    tc::mbar_init(&afull, 4);
+    abort_flag = 0;
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tD = tbase;               // D buffers: columns [0, NB) and [NB, 2 NB)
+  const uint32_t tA = tbase + 2 * NB;      // A: hi in [2 NB, 2 NB + n1p), lo after it
+
+  if (warp == 4) {
+    // ---------------- copy warp: B blocks into the stage ring ----------------
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x) {
+        int sc, nr, kg, nb0, nb1;
+        m1_item(prm, it, sc, nr, kg, nb0, nb1);
+        const int k = prm.kg_k[kg];
+        for (int nb = nb0; nb < nb1 && !abort_flag; ++nb)
+          for (int c = 0; c < G.nkc; ++c, ++cnt) {
+            const int st = cnt % S;
+            if (cnt >= (uint32_t)S && (abort_flag || !tc::mbar_wait(&sempty[st], ((cnt / S) - 1) & 1))) {
+              abort_flag = 1;
+              break;
+            }
+            mbar_arrive_expect_tx(&sfull[st], stage_bytes);
+            bulk_g2s(stages + (size_t)st * stage_bytes, prm.Bop + G.block_u32(k, sc, nb, c), stage_bytes,
+                     &sfull[st]);
+          }
+      }
+      if (abort_flag)  // let the copies in flight land before the CTA exits
+        for (uint32_t c = cnt > (uint32_t)S ? cnt - S : 0; c < cnt; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    // ---------------- MMA warp ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::instr_desc(128, NB, 0);  // kind::f16, f16 operands, FP32 D
+      const uint32_t sbo = (uint32_t)G.KC * 32u;          // 8 rows x KC / 4 pieces of 16 bytes
+      uint32_t cnt = 0, dc = 0, ai = 0;
+      for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x, ++ai) {
+        int sc, nr, kg, nb0, nb1;
+        m1_item(prm, it, sc, nr, kg, nb0, nb1);
+        if (!tc::mbar_wait(&afull, ai & 1)) {
+          abort_flag = 1;
+          break;
+        }
+        tc::fence_after();
+        for (int nb = nb0; nb < nb1 && !abort_flag; ++nb, ++dc) {
+          const int buf = dc & 1;
+          if (dc >= 2 && !tc::mbar_wait(&dempty[buf], ((dc >> 1) - 1) & 1)) {
+            abort_flag = 1;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t d = tD + buf * NB;
+          for (int c = 0; c < G.nkc; ++c, ++cnt) {
+            const int st = cnt % S;
+            if (!tc::mbar_wait(&sfull[st], (cnt / S) & 1)) {
+              abort_flag = 1;
+              break;
+            }
+            tc::fence_after();
+            const int ksn = min(G.KC, G.n1p - c * G.KC) / 8;
+            const uint32_t sb = tc::smem_u32(stages + (size_t)st * stage_bytes);
+            for (int ks = 0; ks < ksn; ++ks) {
+              const uint32_t acol = (uint32_t)(c * G.KC + 8 * ks);
+              const uint64_t bh = tc::smem_desc(sb + ks * 256, 128, sbo);
+              const uint64_t bl = tc::smem_desc(sb + 4u * G.chunk_u32 + ks * 256, 128, sbo);
+              tc::mma_ts(d, tA + acol, bh, idesc, (c | ks) != 0);    // hi . hi
+              tc::mma_ts(d, tA + acol, bl, idesc, 1u);               // hi . lo
+              tc::mma_ts(d, tA + G.n1p + acol, bh, idesc, 1u);       // lo . hi
+            }
+            tc::commit(&sempty[st]);
+          }
+          if (abort_flag) break;
+          tc::commit(&dfull[buf]);
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue warps: A into TMEM, then sum_i23 conj(W) T per row ----------------
+    const int l = warp * 32 + lane;  // row of the group = TMEM lane
+    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+    uint32_t dc = 0;
+    for (int64_t it = blockIdx.x; it < prm.nitems; it += gridDim.x) {
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      int sc, nr, kg, nb0, nb1;
+      m1_item(prm, it, sc, nr, kg, nb0, nb1);
+      const int k = prm.kg_k[kg];
+      // A of group kg; the previous item's MMAs are complete (its last D buffer was drained)
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(prm.A) + (int64_t)kg * 2 * (G.n1p / 4) * kM1Rows + l;
+        for (int cb = 0; cb < 2 * (G.n1p / 4); ++cb) tmem_st4(tA + lanebase + 4 * cb, src[(int64_t)cb * kM1Rows]);
+        tc::tmem_wait_st();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&afull);
+      }
+      const Mode1Row ri = prm.rows[(int64_t)kg * kM1Rows + l];
+      float2 acc[P];
+#pragma unroll
+      for (int s = 0; s < P; ++s) acc[s] = make_float2(0.f, 0.f);
+      for (int nb = nb0; nb < nb1; ++nb, ++dc) {
+        // this row's W values and the block's scale, loaded before the wait; the scale multiplies
+        // the block's sums (not W), so that no intermediate leaves FP32's normal range
+        const int e_blk = prm.Eblk[((int64_t)k * G.nsc + sc) * G.NBT + nb];
+        const float f = ldexpf(1.f, e_blk + ri.uexp - 2 * kHalfShift);
+        float2 w[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          const int i23 = nb * I + i;
+          w[i] = (ri.wbase >= 0 && i23 < G.n23) ? prm.W[ri.wbase + (int64_t)i23 * ri.r1p] : make_float2(0.f, 0.f);
+        }
+        const int buf = dc & 1;
+        const bool ok = !abort_flag && tc::mbar_wait(&dfull[buf], (dc >> 1) & 1);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
+        tc::fence_after();
+        float2 blk[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) blk[s] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(tD + lanebase + buf * NB + c0, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int ci = c0 / 2 + i;  // complex column: (i23l, s)
+            blk[ci % P] = cfma_conj(w[ci / P], make_float2(v[2 * i], v[2 * i + 1]), blk[ci % P]);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+          acc[s].x = fmaf(blk[s].x, f, acc[s].x);
+          acc[s].y = fmaf(blk[s].y, f, acc[s].y);
+        }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&dempty[buf]);
+      }
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      float2* out = prm.partial + ((int64_t)nr * prm.KG * kM1Rows + (int64_t)kg * kM1Rows + l) * prm.ppad + sc * P;
+#pragma unroll
+      for (int s = 0; s < P; ++s) out[s] = acc[s];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicExch(prm.err, 1);
+  if (warp == 0) tc::tmem_dealloc(tbase, prm.tcols);
+}
+
+// Psi'[j, s] = sum_nr sum_k sum_{a < r1} partial[nr][first row of (j, k) + a][s]; fixed order
+__global__ void __launch_bounds__(256) mode1_reduce_kernel(const float2* __restrict__ partial,
+                                                           const int2* __restrict__ colrows, int q, int M, int NR,
+                                                           int64_t rows_all, int ppad, int p,
+                                                           float2* __restrict__ out, int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * p) return;
+  const int j = (int)(e / p), s = (int)(e % p);
+  float2 acc = make_float2(0.f, 0.f);
+  for (int nr = 0; nr < NR; ++nr)
+    for (int k = 0; k < q; ++k) {
+      const int2 cr = colrows[(int64_t)j * q + k];
+      const float2* src = partial + ((int64_t)nr * rows_all + cr.x) * ppad + s;
+      for (int a = 0; a < cr.y; ++a) {
+        const float2 v = src[(int64_t)a * ppad];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+    }
+  out[j + ldo * s] = acc;
+}
+
+template <int P, int NB>
+static int launch_mode1(const M1Params& prm, size_t smem, int grid, cudaStream_t st) {
+  ZBC_TRY((set_smem_limit<rmatvec_mode1_kernel<P, NB>>((int)smem)));
+  rmatvec_mode1_kernel<P, NB><<<grid, kM1Threads, smem, st>>>(prm);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  return ZBC_OK;
+}
+
+template <int P>
+static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo,
+                           cudaStream_t st) {
+  const Mode1Cache& mc = *h.cache->mode1;
+  M1Geo G;
+  G.P = P;
+  G.n1 = h.n1;
+  G.n1p = mc.n1p;
+  G.n23 = h.n2 * h.n3;
+  G.nsc = ceil_div(p, P);
+  // N block: at most 16 values of i23 (the epilogue's W registers) and 128 rows, and room in
+  // TMEM for two D buffers beside A (2 n1p columns)
+  int NB = std::min(128, 32 * P);
+  while (NB > 32 && 2 * NB + 2 * G.n1p > 512) NB /= 2;
+  if (NB < 2 * P || 2 * NB + 2 * G.n1p > 512) {
+    set_error("mode-1 adjoint: n1 = %d does not fit tensor memory (n1 <= %d)", h.n1, kM1MaxN1p);
+    return ZBC_EINVAL;
+  }
+  G.NB = NB;
+  G.I = NB / (2 * P);
+  G.NBT = ceil_div(G.n23, G.I);
+  G.nkc = ceil_div(G.n1p, 32);
+  G.KC = ceil_div(G.n1p / 8, G.nkc) * 8;
+  G.chunk_u32 = (uint32_t)NB * G.KC;
+  const size_t stage_bytes = 8 * (size_t)G.chunk_u32;
+  const size_t budget = 200 * 1024;
+  const int S = (int)std::min<size_t>(kM1MaxStages, (budget - 1024) / stage_bytes);
+  if (S < 2) {
+    set_error("mode-1 adjoint: stage layout does not fit shared memory");
+    return ZBC_EINVAL;
+  }
+  const size_t smem = 1024 + (size_t)S * stage_bytes;
+  // items: N ranges x groups per pass, balanced over one CTA per SM; an item's cost is its
+  // N blocks plus about two for loading A and writing its partial sums
+  const int nsm = sm_count();
+  int NR = 1;
+  double best = 1e300;
+  for (int r = 1; r <= std::min(G.NBT, 64); ++r) {
+    const int64_t items = (int64_t)G.nsc * r * mc.KG;
+    const int64_t per = (items + nsm - 1) / nsm;
+    const double cost = (double)per * ((double)G.NBT / r + 2.0);
+    if (cost < best * 0.999) {
+      best = cost;
+      NR = r;
+    }
+  }
+  const int64_t nitems = (int64_t)G.nsc * NR * mc.KG;
+  const int grid = (int)std::min<int64_t>(nsm, nitems);
+  // workspaces: B operand blocks + block exponents; partial sums
+  const size_t bop_bytes = 4 * (size_t)h.q * G.nsc * G.NBT * G.nkc * 2 * G.chunk_u32;
+  const size_t e_bytes = sizeof(int) * (size_t)h.q * G.nsc * G.NBT;
+  ZBC_TRY(h.work_phi.ensure(bop_bytes + e_bytes));
+  const int ppad = G.nsc * P;
+  const int64_t rows_all = (int64_t)mc.KG * kM1Rows;
+  ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)NR * rows_all * ppad));
+  uint32_t* Bop = (uint32_t*)h.work_phi.ptr;
+  int* Eblk = (int*)((unsigned char*)h.work_phi.ptr + bop_bytes);
+  phi_split_kernel<<<dim3(G.NBT, G.nsc, h.q), 256, 0, st>>>(Phi, ldphi, p, h.nv(), G, Bop, Eblk);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  M1Params prm;
+  prm.A = mc.A;
+  prm.rows = mc.rows;
+  prm.kg_k = mc.kg_k;
+  prm.W = h.cache->data;
+  prm.Bop = Bop;
+  prm.Eblk = Eblk;
+  prm.partial = (float2*)h.work_partial.ptr;
+  prm.err = (int*)h.work_err.ptr;
+  prm.G = G;
+  prm.KG = mc.KG;
+  prm.NR = NR;
+  prm.S = S;
+  prm.ppad = ppad;
+  uint32_t tcols = 32;
+  while (tcols < (uint32_t)(2 * NB + 2 * G.n1p)) tcols <<= 1;
+  prm.tcols = tcols;
+  prm.nitems = nitems;
+  int s;
+  if constexpr (P == 1)
+    s = launch_mode1<P, 32>(prm, smem, grid, st);
+  else if constexpr (P == 2)
+    s = NB == 64 ? launch_mode1<P, 64>(prm, smem, grid, st) : launch_mode1<P, 32>(prm, smem, grid, st);
+  else
+    s = NB == 128  ? launch_mode1<P, 128>(prm, smem, grid, st)
+        : NB == 64 ? launch_mode1<P, 64>(prm, smem, grid, st)
+                   : launch_mode1<P, 32>(prm, smem, grid, st);
+  ZBC_TRY(s);
+  mode1_reduce_kernel<<<ceil_div((int64_t)h.M * p, 256), 256, 0, st>>>((const float2*)h.work_partial.ptr, mc.colrows,
+                                                                       h.q, h.M, NR, rows_all, ppad, p, out, ldo);
+  ZBC_TRY_CUDA(cudaGetLastError());
+  count_launch();
+  return ZBC_OK;
+}
+
+// Psi' = Z^H Phi on the handle's stored columns (M rows of Psi'), mode-1 tensor-core form
+int rmatvec_mode1(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st) {
+  ZBC_TRY(build_mode1_cache(h, st));
+  if (p == 1) return rmatvec_mode1_p<1>(h, Phi, ldphi, p, out, ldo, st);
+  if (p == 2) return rmatvec_mode1_p<2>(h, Phi, ldphi, p, out, ldo, st);
+  if (p <= 4) return rmatvec_mode1_p<4>(h, Phi, ldphi, p, out, ldo, st);
+  if (p <= 8) return rmatvec_mode1_p<8>(h, Phi, ldphi, p, out, ldo, st);
+  return rmatvec_mode1_p<kM1MaxP>(h, Phi, ldphi, p, out, ldo, st);
+}
+
+}  // namespace zbc

@@ -90,6 +90,7 @@ struct Handle {
   DevBuf work_misc;
   DevBuf work_xt;        // X^T of the forward products (s-chunk padded rows)
   DevBuf work_err;       // int: set by a product kernel whose bounded wait gave up
+  DevBuf work_phi;       // mode-1 adjoint: fp16 operand blocks of Phi and their exponents
   TcPack* tc = nullptr;
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
@@ -98,6 +99,7 @@ struct Handle {
   int8_t tune_fwd_prec[kPClasses] = {-1, -1, -1, -1, -1, -1, -1, -1};
   int8_t tune_fwd_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
   int8_t tune_adj_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int8_t tune_adj_prec[kPClasses] = {-1, -1, -1, -1, -1, -1, -1, -1};
   ~Handle();
   int64_t nv() const { return (int64_t)n1 * n2 * n3; }
   int upload();          // copy desc to device (pool already on device)
@@ -158,6 +160,8 @@ int sm_count();
 int matvec_simt(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, int warps, cudaStream_t st);
 int rmatvec_simt(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, int warps,
                  cudaStream_t st);
+// the adjoint with the mode-1 product on the tensor cores (products_mode1.cu)
+int rmatvec_mode1(Handle& h, const float2* Phi, int64_t ldphi, int p, float2* out, int64_t ldo, cudaStream_t st);
 
 // number of kernels this library has launched (all entry points), for launch accounting
 void count_launch(int n = 1);

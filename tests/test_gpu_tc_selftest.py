@@ -15,7 +15,7 @@ __graft_entry__.build()
 from paper_2103_06393_gb300 import zbc  # noqa: E402
 
 
-@pytest.mark.parametrize("fmt", [0, 1, 2])
+@pytest.mark.parametrize("fmt", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("N", [16, 32, 64])
 def test_integer_exact(fmt, N):
     rng = np.random.default_rng(fmt * 100 + N)
@@ -26,14 +26,14 @@ def test_integer_exact(fmt, N):
     assert np.array_equal(D, A @ B.T)
 
 
-@pytest.mark.parametrize("fmt,K", [(0, 16), (1, 64), (2, 8), (2, 64)])
+@pytest.mark.parametrize("fmt,K", [(0, 16), (1, 64), (2, 8), (2, 64), (3, 16), (3, 64), (4, 32)])
 def test_random_against_rounded_host(fmt, K):
     rng = np.random.default_rng(K + fmt)
     A = rng.normal(size=(128, K)).astype(np.float32)
     B = rng.normal(size=(48, K)).astype(np.float32)
-    if fmt == 0:
+    if fmt in (0, 3):
         Ar, Br = A.astype(np.float16).astype(np.float64), B.astype(np.float16).astype(np.float64)
-    elif fmt == 1:
+    elif fmt in (1, 4):
         Ar = torch.from_numpy(A).to(torch.bfloat16).double().numpy()
         Br = torch.from_numpy(B).to(torch.bfloat16).double().numpy()
     else:
