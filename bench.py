@@ -386,7 +386,9 @@ def run_zbc(args):
     # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; only for the full workload
     # and the kernel version it was taken on
     measured_traffic = {("rmatvec_simt_kernel", "adj_simt9"): 3.313e9 + 0.059e9,
-                        ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9}
+                        ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9,
+                        ("matvec_tc_kernel", "fwd_tf32x3"): 2.9106e9 + 0.3299e9,
+                        ("matvec_tc_kernel", "tf32x3"): 2.9106e9 + 0.3299e9}
     dom_variant = variant["forward"] if dom_fwd else variant["adjoint"]
     if not args.columns:
         roof["traffic"] = measured_traffic.get((kern, dom_variant))

@@ -25,9 +25,10 @@
 //   phi_split_kernel      Phi -> the B operand blocks (fp16 hi / lo, one contiguous run per
 //                         (component, RHS chunk, N block, K chunk)) and one exponent per N block
 //   rmatvec_mode1_kernel  persistent, one CTA per SM; items (RHS chunk, N range, group):
-//                         4 epilogue warps (A into TMEM, T . conj(W) sums), a copy warp
+//                         epilogue warps (A into TMEM, T . conj(W) sums), a copy warp
 //                         (cp.async.bulk of the B blocks into a stage ring) and an MMA warp
-//                         (A from TMEM, B from shared memory, D double-buffered in TMEM)
+//                         (A from TMEM, B from shared memory, D in TMEM: N = 256 columns with
+//                         one buffer and two epilogue warpgroups, else two buffers)
 //   mode1_reduce_kernel   Psi'[j, s] = sum over N ranges, components and ranks, fixed order
 // plus, once per handle, mode1_build_kernel (the A operand and the row table).
 #include <cuda_fp16.h>
@@ -41,7 +42,6 @@ namespace zbc {
 constexpr int kM1Rows = 128;       // (column, rank) rows per group = MMA M = TMEM lanes
 constexpr int kM1MaxP = 16;        // right-hand sides per pass
 constexpr int kM1MaxStages = 8;
-constexpr int kM1Threads = 32 * 6;  // 4 epilogue warps, the copy warp, the MMA warp
 constexpr int kM1MaxN1p = 224;     // A (2 n1p TMEM columns) + two D buffers of >= 32 columns
 
 struct Mode1Row {
@@ -169,7 +169,8 @@ int build_mode1_cache(Handle& h, cudaStream_t st) {
 }
 
 // B operand geometry of one call: N blocks of NB rows (I = NB / (2P) values of i23, each with P
-// right-hand sides times (Re, Im) rows), K in nkc chunks of KC i1 (the last may be shorter).
+// right-hand sides times (Re, Im) rows), K in nkc chunks of KC = 32 i1 (64 fp16 = one 128-byte
+// swizzled row; the last chunk's K steps stop at n1p, its tail is zero).
 struct M1Geo {
   int P, NB, I;       // RHS per pass, rows per N block, i23 per N block
   int nsc;            // passes over the right-hand sides (ceil(p / P))
@@ -179,19 +180,25 @@ struct M1Geo {
   __host__ __device__ int64_t block_u32(int k, int sc, int nb, int c) const {
     return ((((int64_t)k * nsc + sc) * NBT + nb) * nkc + c) * 2 * chunk_u32;
   }
+  // exponent of (component, pass, N block, right-hand side of the pass)
+  __host__ __device__ int64_t exp_index(int k, int sc, int nb, int s) const {
+    return (((int64_t)k * nsc + sc) * NBT + nb) * P + s;
+  }
 };
 
-// One CTA per (N block, pass, component): the block's largest |Re|, |Im| fixes its exponent,
-// then each thread writes 16-byte pieces (4 i1 of one row, both terms) in the canonical K-major
-// layout of tc_common.cuh (rows grouped by 8, KC / 4 pieces per row per chunk).
+// One CTA per (N block, pass, component).  The largest |Re|, |Im| of each right-hand side over
+// the block fixes that right-hand side's exponent e (max < 2^e), so right-hand sides of very
+// different magnitudes keep their accuracy; then each thread writes 16-byte pieces (4 i1 of
+// one row, both terms) in the 128-byte swizzled K-major layout (tc::sw128_off; 8 pieces per
+// row per chunk).
 __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict__ Phi, int64_t ldphi, int p,
                                                         int64_t nv, M1Geo G, uint32_t* __restrict__ Bop,
                                                         int* __restrict__ Eblk) {
   const int nb = blockIdx.x, sc = blockIdx.y, k = blockIdx.z;
   const int KB4 = G.KC / 4;
   const int npiece = G.NB * G.nkc * KB4;
-  __shared__ float wmax[8];
-  __shared__ int sexp;
+  __shared__ unsigned int smax[kM1MaxP];  // float bits of non-negative maxima (ordered as integers)
+  __shared__ int sexp[kM1MaxP];
   // piece index -> (chunk c, row n, piece kc within the row's chunk), ordered by output address
   auto decode = [&](int pi, int& c, int& n, int& kc) {
     const int r8 = pi & 7;
@@ -208,33 +215,30 @@ __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict
     off = (int64_t)k * nv + (int64_t)G.n1 * i23 + ldphi * s;
     return i23 < G.n23 && s < p;
   };
-  float mx = 0.f;
+  if (threadIdx.x < kM1MaxP) smax[threadIdx.x] = 0u;
+  __syncthreads();
   for (int pi = threadIdx.x; pi < npiece; pi += blockDim.x) {
     int c, n, kc, i1;
     int64_t off;
     decode(pi, c, n, kc);
     if ((n & 1) || !source(n, c, kc, i1, off)) continue;
+    float mx = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i1 + i < G.n1) {
         const float2 v = Phi[off + i1 + i];
         mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
+    if (mx > 0.f) atomicMax(&smax[(n >> 1) % G.P], __float_as_uint(mx));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+  if (threadIdx.x < G.P) {
     int e = 0;
-    frexpf(m, &e);
-    sexp = e;
-    Eblk[((int64_t)k * G.nsc + sc) * G.NBT + nb] = e;
+    frexpf(__uint_as_float(smax[threadIdx.x]), &e);
+    sexp[threadIdx.x] = e;
+    Eblk[G.exp_index(k, sc, nb, threadIdx.x)] = e;
   }
   __syncthreads();
-  const int sh = kHalfShift - sexp;
   uint32_t* out = Bop + G.block_u32(k, sc, nb, 0);
   for (int pi = threadIdx.x; pi < npiece; pi += blockDim.x) {
     int c, n, kc, i1;
@@ -242,6 +246,7 @@ __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict
     decode(pi, c, n, kc);
     uint32_t hw[4], lw[4];
     const bool ok = source(n, c, kc, i1, off);
+    const int sh = kHalfShift - sexp[(n >> 1) % G.P];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float2 v = (ok && i1 + i < G.n1) ? Phi[off + i1 + i] : make_float2(0.f, 0.f);
@@ -253,8 +258,8 @@ __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict
       hw[i] = *reinterpret_cast<const uint32_t*>(&vh);
       lw[i] = *reinterpret_cast<const uint32_t*>(&vl);
     }
-    // chunk c, term t: (c * 2 + t) * chunk_u32; piece (n, kc) at core_off(n, kc, KB4) bytes
-    const int64_t o = (int64_t)c * 2 * G.chunk_u32 + tc::core_off(n, kc, KB4) / 4;
+    // chunk c, term t: (c * 2 + t) * chunk_u32; piece (n, kc) at sw128_off(n, kc) bytes
+    const int64_t o = (int64_t)c * 2 * G.chunk_u32 + tc::sw128_off(n, kc) / 4;
     *reinterpret_cast<uint4*>(out + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     *reinterpret_cast<uint4*>(out + o + G.chunk_u32) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
@@ -266,6 +271,19 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
                : "memory");
 }
 
+// 16 columns of this thread's TMEM lane, without waiting (tmem_wait_ld completes all of them)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 struct M1Params {
   const uint32_t* A;
   const Mode1Row* rows;
@@ -273,7 +291,7 @@ struct M1Params {
   const float2* W;  // decompression cache
   const uint32_t* Bop;
   const int* Eblk;
-  float2* partial;  // [NR][KG * 128][ppad]
+  float2* partial;  // [NR * EG slots][KG * 128][ppad]
   int* err;
   M1Geo G;
   int KG, NR, S, ppad;
@@ -293,9 +311,26 @@ __device__ __forceinline__ void m1_item(const M1Params& prm, int64_t it, int& sc
   nb1 = (int)((int64_t)prm.G.NBT * (nr + 1) / prm.NR);
 }
 
+// Shape of the main kernel for NB rows per N block: two D buffers while they fit beside A in
+// tensor memory (NB <= 160 for n1 <= 96), else one 256-column buffer drained by two epilogue
+// warpgroups at once (each takes half of its columns), so that it is handed back after a single
+// round of TMEM loads.  Fewer, larger MMAs are what matters: the MMA issue costs about the same
+// per instruction for 128 and 160 columns.
+template <int NB>
+struct M1Shape {
+  static constexpr int DB = NB > 160 ? 1 : 2;       // D buffers
+  static constexpr int EG = NB > 160 ? 2 : 1;       // epilogue warpgroups
+  static constexpr int threads = 32 * (4 * EG + 2);  // + the copy warp and the MMA warp
+};
+
 template <int P, int NB>
-__global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Params prm) {
-  constexpr int I = NB / (2 * P);  // i23 per N block
+__global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(const M1Params prm) {
+  using Sh = M1Shape<NB>;
+  constexpr int DB = Sh::DB, EG = Sh::EG;
+  constexpr int I = NB / (2 * P);     // i23 per N block
+  constexpr int NC = NB / EG;         // D columns per epilogue warpgroup
+  constexpr int IW = NC / (2 * P) > 0 ? NC / (2 * P) : 1;  // i23 per warpgroup
+  static_assert(NC % (2 * P) == 0, "a warpgroup's columns are whole i23 values");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t sfull[kM1MaxStages], sempty[kM1MaxStages], dfull[2], dempty[2], afull;
   __shared__ uint32_t tbase;
@@ -305,6 +340,7 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
   const int S = prm.S;
   const uint32_t stage_bytes = 8u * G.chunk_u32;  // both terms of one K chunk
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int copy_warp = 4 * EG, mma_warp = 4 * EG + 1;
 
   if (warp == 0) tc::tmem_alloc(&tbase, prm.tcols);
   if (threadIdx.x == 0) {
@@ -314,18 +350,18 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&dfull[b], 1);
-      tc::mbar_init(&dempty[b], 4);
+      tc::mbar_init(&dempty[b], 4 * EG);
     }
-    tc::mbar_init(&afull, 4);
+    tc::mbar_init(&afull, 4 * EG);
     abort_flag = 0;
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tD = tbase;               // D buffers: columns [0, NB) and [NB, 2 NB)
-  const uint32_t tA = tbase + 2 * NB;      // A: hi in [2 NB, 2 NB + n1p), lo after it
+  const uint32_t tD = tbase;               // D buffers: columns [b NB, (b + 1) NB)
+  const uint32_t tA = tbase + DB * NB;     // A: hi in [DB NB, DB NB + n1p), lo after it
 
-  if (warp == 4) {
+  if (warp == copy_warp) {
     // ---------------- copy warp: B blocks into the stage ring ----------------
     if (lane == 0) {
       uint32_t cnt = 0;
@@ -349,11 +385,10 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
         for (uint32_t c = cnt > (uint32_t)S ? cnt - S : 0; c < cnt; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
     }
     __syncwarp();
-  } else if (warp == 5) {
+  } else if (warp == mma_warp) {
     // ---------------- MMA warp ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::instr_desc(128, NB, 0);  // kind::f16, f16 operands, FP32 D
-      const uint32_t sbo = (uint32_t)G.KC * 32u;          // 8 rows x KC / 4 pieces of 16 bytes
       uint32_t cnt = 0, dc = 0, ai = 0;
       for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x, ++ai) {
         int sc, nr, kg, nb0, nb1;
@@ -364,8 +399,9 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
         }
         tc::fence_after();
         for (int nb = nb0; nb < nb1 && !abort_flag; ++nb, ++dc) {
-          const int buf = dc & 1;
-          if (dc >= 2 && !tc::mbar_wait(&dempty[buf], ((dc >> 1) - 1) & 1)) {
+          const int buf = dc % DB;
+          const uint32_t use = dc / DB;  // the use-th fill of this D buffer
+          if (use >= 1 && !tc::mbar_wait(&dempty[buf], (use - 1) & 1)) {
             abort_flag = 1;
             break;
           }
@@ -382,8 +418,8 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
             const uint32_t sb = tc::smem_u32(stages + (size_t)st * stage_bytes);
             for (int ks = 0; ks < ksn; ++ks) {
               const uint32_t acol = (uint32_t)(c * G.KC + 8 * ks);
-              const uint64_t bh = tc::smem_desc(sb + ks * 256, 128, sbo);
-              const uint64_t bl = tc::smem_desc(sb + 4u * G.chunk_u32 + ks * 256, 128, sbo);
+              const uint64_t bh = tc::smem_desc_sw128(sb + ks * 32);
+              const uint64_t bl = tc::smem_desc_sw128(sb + 4u * G.chunk_u32 + ks * 32);
               tc::mma_ts(d, tA + acol, bh, idesc, (c | ks) != 0);    // hi . hi
               tc::mma_ts(d, tA + acol, bl, idesc, 1u);               // hi . lo
               tc::mma_ts(d, tA + G.n1p + acol, bh, idesc, 1u);       // lo . hi
@@ -398,18 +434,30 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
     __syncwarp();
   } else {
     // ---------------- epilogue warps: A into TMEM, then sum_i23 conj(W) T per row ----------------
-    const int l = warp * 32 + lane;  // row of the group = TMEM lane
-    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+    const int eg = warp / 4;                  // epilogue warpgroup: D columns [eg NC, (eg + 1) NC)
+    const int l = (warp % 4) * 32 + lane;     // row of the group = TMEM lane
+    const uint32_t lanebase = (uint32_t)((warp % 4) * 32) << 16;
     uint32_t dc = 0;
     for (int64_t it = blockIdx.x; it < prm.nitems; it += gridDim.x) {
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
       int sc, nr, kg, nb0, nb1;
       m1_item(prm, it, sc, nr, kg, nb0, nb1);
       const int k = prm.kg_k[kg];
-      // A of group kg; the previous item's MMAs are complete (its last D buffer was drained)
+      // A of group kg, the warpgroups splitting its columns; the previous item's MMAs are complete
+      // (its last D fill was drained, and that fill's commit came after all of them)
       {
         const uint4* src = reinterpret_cast<const uint4*>(prm.A) + (int64_t)kg * 2 * (G.n1p / 4) * kM1Rows + l;
-        for (int cb = 0; cb < 2 * (G.n1p / 4); ++cb) tmem_st4(tA + lanebase + 4 * cb, src[(int64_t)cb * kM1Rows]);
+        const int ncb = 2 * (G.n1p / 4);
+        const int cb_lo = ncb * eg / EG, cb_hi = ncb * (eg + 1) / EG;
+        for (int cb0 = cb_lo; cb0 < cb_hi; cb0 += 8) {  // 8 loads in flight, then their stores
+          uint4 v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (cb0 + i < cb_hi) v[i] = __ldg(src + (int64_t)(cb0 + i) * kM1Rows);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (cb0 + i < cb_hi) tmem_st4(tA + lanebase + 4 * (cb0 + i), v[i]);
+        }
         tc::tmem_wait_st();
         tc::fence_before();
         __syncwarp();
@@ -420,47 +468,59 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
 #pragma unroll
       for (int s = 0; s < P; ++s) acc[s] = make_float2(0.f, 0.f);
       for (int nb = nb0; nb < nb1; ++nb, ++dc) {
-        // this row's W values and the block's scale, loaded before the wait; the scale multiplies
-        // the block's sums (not W), so that no intermediate leaves FP32's normal range
-        const int e_blk = prm.Eblk[((int64_t)k * G.nsc + sc) * G.NBT + nb];
-        const float f = ldexpf(1.f, e_blk + ri.uexp - 2 * kHalfShift);
-        float2 w[I];
+        // this row's W values and the block's scales, loaded before the wait; a scale multiplies
+        // each product (not W), so that no intermediate leaves FP32's normal range
+        float f[P];
 #pragma unroll
-        for (int i = 0; i < I; ++i) {
-          const int i23 = nb * I + i;
+        for (int s = 0; s < P; ++s)
+          f[s] = ldexpf(1.f, prm.Eblk[G.exp_index(k, sc, nb, s)] + ri.uexp - 2 * kHalfShift);
+        float2 w[IW];
+#pragma unroll
+        for (int i = 0; i < IW; ++i) {
+          const int i23 = nb * I + eg * IW + i;
           w[i] = (ri.wbase >= 0 && i23 < G.n23) ? prm.W[ri.wbase + (int64_t)i23 * ri.r1p] : make_float2(0.f, 0.f);
         }
-        const int buf = dc & 1;
-        const bool ok = !abort_flag && tc::mbar_wait(&dfull[buf], (dc >> 1) & 1);
+        const int buf = dc % DB;
+        const bool ok = !abort_flag && tc::mbar_wait(&dfull[buf], (dc / DB) & 1);
         if (!__all_sync(0xffffffffu, ok)) {
           if (lane == 0) abort_flag = 1;
           break;
         }
         tc::fence_after();
-        float2 blk[P];
+        // this warpgroup's D columns in registers, in rounds of loads that fit the registers; with
+        // one D buffer it is handed back as soon as the last round is loaded
+        constexpr int kBatch = EG == 2 ? 64 : (NC > 128 ? 96 : NC);
 #pragma unroll
-        for (int s = 0; s < P; ++s) blk[s] = make_float2(0.f, 0.f);
+        for (int b0 = 0; b0 < NC; b0 += kBatch) {
+          float v[kBatch];
 #pragma unroll
-        for (int c0 = 0; c0 < NB; c0 += 16) {
-          float v[16];
-          tc::tmem_ld16(tD + lanebase + buf * NB + c0, v);
+          for (int c0 = 0; c0 < kBatch; c0 += 16)
+            if (b0 + c0 < NC) tmem_ld16_nowait(tD + lanebase + buf * NB + eg * NC + b0 + c0, v + c0);
+          tmem_wait_ld();
+          if (DB == 1 && b0 + kBatch >= NC) {
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&dempty[buf]);
+          }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int ci = c0 / 2 + i;  // complex column: (i23l, s)
-            blk[ci % P] = cfma_conj(w[ci / P], make_float2(v[2 * i], v[2 * i + 1]), blk[ci % P]);
+          for (int cc = 0; cc < kBatch / 2; ++cc) {
+            const int ci = b0 / 2 + cc;  // complex column of the warpgroup: (i23 offset, s)
+            if (ci < NC / 2) {
+              const float2 t = cfma_conj(w[ci / P], make_float2(v[2 * cc], v[2 * cc + 1]), make_float2(0.f, 0.f));
+              acc[ci % P].x = fmaf(t.x, f[ci % P], acc[ci % P].x);
+              acc[ci % P].y = fmaf(t.y, f[ci % P], acc[ci % P].y);
+            }
           }
         }
-#pragma unroll
-        for (int s = 0; s < P; ++s) {
-          acc[s].x = fmaf(blk[s].x, f, acc[s].x);
-          acc[s].y = fmaf(blk[s].y, f, acc[s].y);
+        if (DB == 2) {
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive1(&dempty[buf]);
         }
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive1(&dempty[buf]);
       }
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-      float2* out = prm.partial + ((int64_t)nr * prm.KG * kM1Rows + (int64_t)kg * kM1Rows + l) * prm.ppad + sc * P;
+      float2* out = prm.partial +
+                    ((int64_t)(nr * EG + eg) * prm.KG * kM1Rows + (int64_t)kg * kM1Rows + l) * prm.ppad + sc * P;
 #pragma unroll
       for (int s = 0; s < P; ++s) out[s] = acc[s];
     }
@@ -471,19 +531,19 @@ __global__ void __launch_bounds__(kM1Threads, 1) rmatvec_mode1_kernel(const M1Pa
   if (warp == 0) tc::tmem_dealloc(tbase, prm.tcols);
 }
 
-// Psi'[j, s] = sum_nr sum_k sum_{a < r1} partial[nr][first row of (j, k) + a][s]; fixed order
+// Psi'[j, s] = sum over partial slots, components and ranks of (j, k); fixed order
 __global__ void __launch_bounds__(256) mode1_reduce_kernel(const float2* __restrict__ partial,
-                                                           const int2* __restrict__ colrows, int q, int M, int NR,
+                                                           const int2* __restrict__ colrows, int q, int M, int nslots,
                                                            int64_t rows_all, int ppad, int p,
                                                            float2* __restrict__ out, int64_t ldo) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)M * p) return;
   const int j = (int)(e / p), s = (int)(e % p);
   float2 acc = make_float2(0.f, 0.f);
-  for (int nr = 0; nr < NR; ++nr)
+  for (int sl = 0; sl < nslots; ++sl)
     for (int k = 0; k < q; ++k) {
       const int2 cr = colrows[(int64_t)j * q + k];
-      const float2* src = partial + ((int64_t)nr * rows_all + cr.x) * ppad + s;
+      const float2* src = partial + ((int64_t)sl * rows_all + cr.x) * ppad + s;
       for (int a = 0; a < cr.y; ++a) {
         const float2 v = src[(int64_t)a * ppad];
         acc.x += v.x;
@@ -494,12 +554,24 @@ __global__ void __launch_bounds__(256) mode1_reduce_kernel(const float2* __restr
 }
 
 template <int P, int NB>
-static int launch_mode1(const M1Params& prm, size_t smem, int grid, cudaStream_t st) {
-  ZBC_TRY((set_smem_limit<rmatvec_mode1_kernel<P, NB>>((int)smem)));
-  rmatvec_mode1_kernel<P, NB><<<grid, kM1Threads, smem, st>>>(prm);
+static int launch_mode1(const M1Params& prm, size_t smem, size_t budget, int grid, cudaStream_t st) {
+  // the limit is set once per device: to the budget, which every launch's size stays within
+  ZBC_TRY((set_smem_limit<rmatvec_mode1_kernel<P, NB>>((int)budget)));
+  rmatvec_mode1_kernel<P, NB><<<grid, M1Shape<NB>::threads, smem, st>>>(prm);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;
+}
+
+// rows per N block for P right-hand sides per pass and A of 2 n1p TMEM columns: the widest MMA
+// that fits (256 columns, one D buffer; else 160 or a power of two, two D buffers), at most 16
+// values of i23 per block (the epilogue's W registers)
+static int mode1_nb(int P, int n1p) {
+  if (P >= 8 && 256 + 2 * n1p <= 512) return 256;
+  if (P >= 8 && 2 * 160 + 2 * n1p <= 512) return 160;
+  int NB = std::min(128, 32 * P);
+  while (NB > 32 && 2 * NB + 2 * n1p > 512) NB /= 2;
+  return NB;
 }
 
 template <int P>
@@ -512,11 +584,9 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   G.n1p = mc.n1p;
   G.n23 = h.n2 * h.n3;
   G.nsc = ceil_div(p, P);
-  // N block: at most 16 values of i23 (the epilogue's W registers) and 128 rows, and room in
-  // TMEM for two D buffers beside A (2 n1p columns)
-  int NB = std::min(128, 32 * P);
-  while (NB > 32 && 2 * NB + 2 * G.n1p > 512) NB /= 2;
-  if (NB < 2 * P || 2 * NB + 2 * G.n1p > 512) {
+  const int NB = mode1_nb(P, G.n1p);
+  const int DB = NB > 160 ? 1 : 2, EG = NB > 160 ? 2 : 1;
+  if (NB < 2 * P || DB * NB + 2 * G.n1p > 512) {
     set_error("mode-1 adjoint: n1 = %d does not fit tensor memory (n1 <= %d)", h.n1, kM1MaxN1p);
     return ZBC_EINVAL;
   }
@@ -524,10 +594,10 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   G.I = NB / (2 * P);
   G.NBT = ceil_div(G.n23, G.I);
   G.nkc = ceil_div(G.n1p, 32);
-  G.KC = ceil_div(G.n1p / 8, G.nkc) * 8;
+  G.KC = 32;
   G.chunk_u32 = (uint32_t)NB * G.KC;
   const size_t stage_bytes = 8 * (size_t)G.chunk_u32;
-  const size_t budget = 200 * 1024;
+  const size_t budget = 225 * 1024;  // 7 stages of 32 KB, 5 of 40 KB or 3 of 64 KB, and the alignment slack
   const int S = (int)std::min<size_t>(kM1MaxStages, (budget - 1024) / stage_bytes);
   if (S < 2) {
     set_error("mode-1 adjoint: stage layout does not fit shared memory");
@@ -550,13 +620,14 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   }
   const int64_t nitems = (int64_t)G.nsc * NR * mc.KG;
   const int grid = (int)std::min<int64_t>(nsm, nitems);
-  // workspaces: B operand blocks + block exponents; partial sums
+  // workspaces: B operand blocks + exponents; partial sums (one slot per N range and warpgroup)
   const size_t bop_bytes = 4 * (size_t)h.q * G.nsc * G.NBT * G.nkc * 2 * G.chunk_u32;
-  const size_t e_bytes = sizeof(int) * (size_t)h.q * G.nsc * G.NBT;
+  const size_t e_bytes = sizeof(int) * (size_t)h.q * G.nsc * G.NBT * P;
   ZBC_TRY(h.work_phi.ensure(bop_bytes + e_bytes));
   const int ppad = G.nsc * P;
   const int64_t rows_all = (int64_t)mc.KG * kM1Rows;
-  ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)NR * rows_all * ppad));
+  const int nslots = NR * EG;
+  ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)nslots * rows_all * ppad));
   uint32_t* Bop = (uint32_t*)h.work_phi.ptr;
   int* Eblk = (int*)((unsigned char*)h.work_phi.ptr + bop_bytes);
   phi_split_kernel<<<dim3(G.NBT, G.nsc, h.q), 256, 0, st>>>(Phi, ldphi, p, h.nv(), G, Bop, Eblk);
@@ -577,21 +648,27 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   prm.S = S;
   prm.ppad = ppad;
   uint32_t tcols = 32;
-  while (tcols < (uint32_t)(2 * NB + 2 * G.n1p)) tcols <<= 1;
+  while (tcols < (uint32_t)(DB * NB + 2 * G.n1p)) tcols <<= 1;
   prm.tcols = tcols;
   prm.nitems = nitems;
   int s;
   if constexpr (P == 1)
-    s = launch_mode1<P, 32>(prm, smem, grid, st);
+    s = launch_mode1<P, 32>(prm, smem, budget, grid, st);
   else if constexpr (P == 2)
-    s = NB == 64 ? launch_mode1<P, 64>(prm, smem, grid, st) : launch_mode1<P, 32>(prm, smem, grid, st);
+    s = NB == 64 ? launch_mode1<P, 64>(prm, smem, budget, grid, st) : launch_mode1<P, 32>(prm, smem, budget, grid, st);
+  else if constexpr (P == 4)
+    s = NB == 128  ? launch_mode1<P, 128>(prm, smem, budget, grid, st)
+        : NB == 64 ? launch_mode1<P, 64>(prm, smem, budget, grid, st)
+                   : launch_mode1<P, 32>(prm, smem, budget, grid, st);
   else
-    s = NB == 128  ? launch_mode1<P, 128>(prm, smem, grid, st)
-        : NB == 64 ? launch_mode1<P, 64>(prm, smem, grid, st)
-                   : launch_mode1<P, 32>(prm, smem, grid, st);
+    s = NB == 256   ? launch_mode1<P, 256>(prm, smem, budget, grid, st)
+        : NB == 160 ? launch_mode1<P, 160>(prm, smem, budget, grid, st)
+        : NB == 128 ? launch_mode1<P, 128>(prm, smem, budget, grid, st)
+        : NB == 64  ? launch_mode1<P, 64>(prm, smem, budget, grid, st)
+                    : launch_mode1<P, 32>(prm, smem, budget, grid, st);
   ZBC_TRY(s);
   mode1_reduce_kernel<<<ceil_div((int64_t)h.M * p, 256), 256, 0, st>>>((const float2*)h.work_partial.ptr, mc.colrows,
-                                                                       h.q, h.M, NR, rows_all, ppad, p, out, ldo);
+                                                                       h.q, h.M, nslots, rows_all, ppad, p, out, ldo);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;

@@ -29,6 +29,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// descriptor of a K-major operand in the 128-byte swizzled layout: rows of 128 bytes, 8-row
+// atoms of 1024 bytes (1024-byte aligned), the 16-byte chunk c of row r stored at chunk
+// c ^ (r % 8); SBO = 1024 between atoms, LBO unused; a K step of 32 bytes advances the start.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;               // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // SBO
+  d |= (uint64_t)1 << 46;               // version
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+// byte offset of (row r, 16-byte chunk c) in the 128-byte swizzled K-major layout
+__host__ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t c) {
+  return (r >> 3) * 1024u + (r & 7u) * 128u + ((c ^ (r & 7u)) << 4);
+}
+
 // instruction descriptor, dense, FP32 accumulator, both operands K-major.
 // fmt: kind::f16 -> 0 = f16, 1 = bf16; kind::tf32 -> 2.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N, int fmt) {

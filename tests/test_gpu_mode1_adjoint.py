@@ -128,9 +128,10 @@ def test_mode1_aca_storage():
     assert rel_cols(P, Po).max() < RTOL
 
 
-@pytest.mark.parametrize("scale", [1e-30, 1e-6, 1e6, 1e30])
+@pytest.mark.parametrize("scale", [1e-20, 1e-6, 1e6, 1e30])
 def test_mode1_extreme_scales(scale):
-    # each N block of Phi is brought into fp16's range by its own power of two
+    # each N block of Phi is brought into fp16's range by its own powers of two; the scales keep
+    # Psi (~1e-8 scale at this voxel size) inside FP32's normal range, as any FP32 form needs
     w = inputs.scaled_workload("precision", (24, 12, 10), m=6)
     h, tens = _handle(w, 1e-6)
     P, Po = _adj(h, w.grid.shape, tens, 4, seed=13, scale=scale)
@@ -148,6 +149,22 @@ def test_mode1_mixed_block_scales():
     Phi[: nv // 3] *= 1e12
     Phi = Phi.astype(np.complex64)
     Psi = zbc.colmajor(len(tens), 2, torch.complex64)
+    zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, zbc.TC_MODE1)
+    zbc.zbc_product_status(h)
+    Po = products.rmatvec(tens, n, Phi.astype(np.complex128))
+    assert rel_cols(zbc.from_colmajor(Psi), Po).max() < RTOL
+
+
+def test_mode1_mixed_column_scales():
+    # right-hand sides 1e40 apart in one pass: each gets its own exponent per N block
+    n = (24, 12, 10)
+    w = inputs.scaled_workload("precision", n, m=5)
+    h, tens = _handle(w, 1e-6)
+    nv = int(np.prod(n))
+    Phi = inputs.cn01((3 * nv, 16), seed=22).astype(np.complex128)
+    Phi *= np.array([1e-20, 1e20, 1.0, 3e-5] * 4)[None, :]
+    Phi = Phi.astype(np.complex64)
+    Psi = zbc.colmajor(len(tens), 16, torch.complex64)
     zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, zbc.TC_MODE1)
     zbc.zbc_product_status(h)
     Po = products.rmatvec(tens, n, Phi.astype(np.complex128))
