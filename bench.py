@@ -199,17 +199,27 @@ def time_steps(fn, steps, flush, torch, stream):
     return times
 
 
-def mode1_gemm_flops(h, w, p):
-    """Real tensor-core flops of the mode-1 adjoint's GEMMs: per group of 128 (column, rank) rows
-    of one component, M = 128, K = 2 n1 (Re, Im of each i1), N = 2 n2 n3 P per pass of P <= 16
-    right-hand sides, times 3 fp16 products (hi.hi, hi.lo, lo.hi)."""
+def mode1_gemm_flops(h, w, p, forward=False):
+    """Real tensor-core flops of the mode-1 form's GEMMs, 3 fp16 products (hi.hi, hi.lo, lo.hi)
+    per real MAC.  Adjoint: per group of 128 (column, rank) rows of one component, M = 128,
+    K = 2 n1p (n1 rounded up to 8), N = 2 n2 n3 P per pass of P <= 16 right-hand sides.
+    Forward: per block of 128 (i23, s) rows, M = 128, N = 2 n1f (n1 rounded up to 16),
+    K = 2 x the component's rows rounded up to chunks of 32."""
     g = w.grid
     ranks = h.export()[0]                      # (M, q, 3)
+    n2n3 = g.shape[1] * g.shape[2]
+    if forward:
+        P = 16 if p > 8 else 8
+        nsc = -(-p // P)
+        blocks = -(-n2n3 // (128 // P)) * nsc
+        rows = sum(-(-int(ranks[:, k, 0].sum()) // 32) * 32 for k in range(ranks.shape[1]))
+        n1f = -(-g.shape[0] // 16) * 16
+        return 2.0 * 128 * (2 * n1f) * (2 * rows) * 3 * blocks
     groups = sum(-(-int(ranks[:, k, 0].sum()) // 128) for k in range(ranks.shape[1]))
     P = 1 << max(0, (min(p, 16) - 1).bit_length())
     nsc = -(-p // P)
     n1p = -(-g.shape[0] // 8) * 8
-    return 2.0 * 128 * (2 * n1p) * (2 * g.shape[1] * g.shape[2] * P * nsc) * 3 * groups
+    return 2.0 * 128 * (2 * n1p) * (2 * n2n3 * P * nsc) * 3 * groups
 
 
 def run_zbc(args):
@@ -259,7 +269,7 @@ def run_zbc(args):
                 pass
         return [c for c in out if args.prec in ("auto", names[c])] or [zbc.FP32_SIMT]
 
-    fwd_codes = available(zbc.zbc_matvec, Xd, Yd, (zbc.TF32X3, zbc.BF16X3, zbc.TC2))
+    fwd_codes = available(zbc.zbc_matvec, Xd, Yd, (zbc.TF32X3, zbc.BF16X3, zbc.TC2, zbc.TC_MODE1))
     adj_codes = available(zbc.zbc_rmatvec, Phid, Psid, (zbc.TC_MODE1,))
     tens, _ = h.tensors()
     nt = max(3, args.steps // 2)
@@ -289,7 +299,7 @@ def run_zbc(args):
     if args.prec == "auto":
         fv = min((k for k in tune if k.startswith("fwd_")), key=lambda k: tune[k])
         av = min((k for k in tune if k.startswith("adj_")), key=lambda k: tune[k])
-        fwd_head = "fp32_simt" if "simt" in fv else fv[4:]
+        fwd_head = "fp32_simt" if "simt" in fv else ("tc_mode1" if fv == "fwd_mode1" else fv[4:])
         adj_head = "fp32_simt" if "simt" in av else "tc_" + av[4:]
         fcode = acode = zbc.AUTO
         variant = {"forward": fv, "adjoint": av}
@@ -377,11 +387,13 @@ def run_zbc(args):
                 "peak_source": f"measured bf16 {bf} TFLOP/s / {mult:.0f} real products per split MAC",
                 "kernel": kern, "traffic": None}
         if dom_name == "tc_mode1":
-            # the mode-1 form's own GEMM (T = U1^H Phi per group of 128 rows, 3 fp16 products)
-            gf = mode1_gemm_flops(h, w, p)
+            # the mode-1 form's own GEMM (3 fp16 products per real MAC)
+            gf = mode1_gemm_flops(h, w, p, forward=dom_fwd)
             roof["gemm"] = {"tflops": gf / (dom_ms * 1e-3) / 1e12, "peak": bf,
                             "frac": gf / (dom_ms * 1e-3) / 1e12 / bf,
-                            "counts": "2 x 128 rows x 2 n1 x 2 (n2 n3 p) x 3 products per group"}
+                            "counts": ("forward: 2 x 128 (i23, s) rows x 2 n1f x 2 (rank rows) x 3 products per block"
+                                       if dom_fwd else
+                                       "adjoint: 2 x 128 (column, rank) rows x 2 n1p x 2 (n2 n3 p) x 3 products per group")}
     # DRAM bytes per launch of the dominant kernel on this workload, from a one-pass ncu capture
     # (dram__bytes_read.sum + dram__bytes_write.sum) of this command; only for the full workload
     # and the kernel version it was taken on

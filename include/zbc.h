@@ -60,11 +60,13 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  * TC2       : (forward only) the last mode product of the decompression on the tensor cores
  *             too: Z = U1 W per column as a tcgen05 MMA with fp16 hi+lo operands (W scaled by a
  *             power of two per tensor), chained through TMEM into the BF16X3 contraction.
- * TC_MODE1  : (adjoint only) Psi = Z^H Phi regrouped so that the mode-1 product is one dense
- *             tcgen05 GEMM per group of 128 (column, rank) rows: T = U1^H Phi^k on the tensor
- *             cores (fp16 hi+lo operands, scaled by powers of two, 3 products, FP32
- *             accumulation), then Psi_j = sum conj(W) T over (rank, i2, i3) on CUDA cores.
- *             Needs n1 <= 224.
+ * TC_MODE1  : the products regrouped so that the mode-1 product is a dense tcgen05 GEMM
+ *             (fp16 hi+lo operands scaled by powers of two, 3 products, FP32 accumulation).
+ *             Adjoint: T = U1^H Phi^k per group of 128 (column, rank) rows, then
+ *             Psi_j = sum conj(W) T over (rank, i2, i3) on CUDA cores; needs n1 <= 224.
+ *             Forward: per block of 128 (i2 i3, RHS) rows, Y^k = U1 (W X) over all (column,
+ *             rank) rows, W X generated on CUDA cores, the tensor-core sum folded into FP32
+ *             every 96 rows; needs n1 <= 96 and p >= 5.
  * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
  *             right-hand-side class; before any tuning, BF16X3 for the forward product when
  *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,
@@ -292,11 +294,11 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
 /*
  * zbc_tune -- autotuner of the product kernels (no counterpart in the paper).  Times, on this
  * handle with p right-hand sides (zero-filled scratch operands), every variant of
- *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2
+ *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2, TC_MODE1
  *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA, TC_MODE1
  * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
  * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the faster SIMT shape).
- *   times_ms_host : optional float[8], the variants' times in the order above (ms per call;
+ *   times_ms_host : optional float[9], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
  */

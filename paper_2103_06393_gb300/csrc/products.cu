@@ -8,6 +8,7 @@ namespace zbc {
 int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, zbc_precision prec,
               cudaStream_t st);
 int matvec_tc2(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
+int matvec_mode1(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
 int aca_pre(const Handle& h, const float2* X, int64_t ldx, int p, float2* Xp, cudaStream_t st);
 int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ldpsi, cudaStream_t st);
 
@@ -24,6 +25,7 @@ static int matvec_impl(Handle& h, const float2* X, int64_t ldx, int p, float2* Y
   }
   if (prec == ZBC_FP32_SIMT) return matvec_simt(h, Xe, ldxe, p, Y, ldy, warps, st);
   if (prec == ZBC_TC2) return matvec_tc2(h, Xe, ldxe, p, Y, ldy, st);
+  if (prec == ZBC_TC_MODE1) return matvec_mode1(h, Xe, ldxe, p, Y, ldy, st);
   return matvec_tc(h, Xe, ldxe, p, Y, ldy, prec, st);
 }
 
@@ -59,7 +61,6 @@ extern "C" int zbc_matvec(const zbc_handle* hh, const void* X, int64_t ldx, int 
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
                     prec == ZBC_TC2 || prec == ZBC_TC_MODE1,
                 "unknown precision %d", (int)prec);
-  ZBC_CHECK_ARG(prec != ZBC_TC_MODE1, "ZBC_TC_MODE1 is a form of the adjoint product only");
   const int cls = rhs_class(p);
   int warps = h.tune_fwd_warps[cls];
   if (prec == ZBC_AUTO)
@@ -108,10 +109,10 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
     zbc_precision prec;
     int warps;
   };
-  constexpr int NV = 8;
-  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6},  {true, ZBC_FP32_SIMT, 9},  {true, ZBC_TF32X3, 0},
-                            {true, ZBC_BF16X3, 0},     {true, ZBC_TC2, 0},        {false, ZBC_FP32_SIMT, 6},
-                            {false, ZBC_FP32_SIMT, 9}, {false, ZBC_TC_MODE1, 0}};
+  constexpr int NV = 9, NF = 6;  // the first NF variants are forward forms
+  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6},  {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
+                            {true, ZBC_BF16X3, 0},     {true, ZBC_TC2, 0},       {true, ZBC_TC_MODE1, 0},
+                            {false, ZBC_FP32_SIMT, 6}, {false, ZBC_FP32_SIMT, 9}, {false, ZBC_TC_MODE1, 0}};
   float t[NV];
   int status = ZBC_OK;
   for (int i = 0; i < NV && status == ZBC_OK; ++i) {
@@ -144,22 +145,21 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != ZBC_OK) return status;
-  if (!(t[0] < INFINITY || t[1] < INFINITY || t[2] < INFINITY || t[3] < INFINITY || t[4] < INFINITY) ||
-      !(t[5] < INFINITY || t[6] < INFINITY || t[7] < INFINITY)) {
+  int bf = 0, ba = NF;
+  for (int i = 1; i < NF; ++i)
+    if (t[i] < t[bf]) bf = i;
+  for (int i = NF + 1; i < NV; ++i)
+    if (t[i] < t[ba]) ba = i;
+  if (!(t[bf] < INFINITY) || !(t[ba] < INFINITY)) {
     set_error("zbc_tune: no product form fits this handle");
     return ZBC_EINVAL;
   }
   const int cls = rhs_class(p);
-  int bf = 0, ba = 5;
-  for (int i = 1; i < 5; ++i)
-    if (t[i] < t[bf]) bf = i;
-  for (int i = 6; i < NV; ++i)
-    if (t[i] < t[ba]) ba = i;
   h.tune_fwd_prec[cls] = (int8_t)vars[bf].prec;
   h.tune_fwd_warps[cls] = (int8_t)vars[bf].warps;
   h.tune_adj_prec[cls] = (int8_t)vars[ba].prec;
   // the SIMT CTA shape stays the faster of the two SIMT variants (zbc_rmatvec_noalloc uses it)
-  h.tune_adj_warps[cls] = (int8_t)(t[6] < t[5] ? 9 : 6);
+  h.tune_adj_warps[cls] = (int8_t)(t[NF + 1] < t[NF] ? 9 : 6);
   if (times_ms_host)
     for (int i = 0; i < NV; ++i) times_ms_host[i] = t[i];
   return ZBC_OK;

@@ -35,38 +35,15 @@
 
 #include <algorithm>
 
-#include "stage.cuh"
+#include "mode1.cuh"
 
 namespace zbc {
 
-constexpr int kM1Rows = 128;       // (column, rank) rows per group = MMA M = TMEM lanes
-constexpr int kM1MaxP = 16;        // right-hand sides per pass
-constexpr int kM1MaxStages = 8;
-constexpr int kM1MaxN1p = 224;     // A (2 n1p TMEM columns) + two D buffers of >= 32 columns
-
-struct Mode1Row {
-  int64_t wbase;  // W_{kj}[i23 = 0, a] in the decompression cache; -1 for a padding row
-  int r1p;        // W's stride per i23
-  int uexp;       // max |Re|, |Im| of U1_{kj}[:, a] < 2^uexp (set by the build kernel)
-};
-
-struct Mode1Cache {
-  int KG = 0;                 // groups over all components
-  int n1p = 0;                // n1 rounded up to 8 (K = 2 n1p reals)
-  uint32_t* A = nullptr;      // [KG][2 terms][n1p / 4][128 rows][4] fp16x2 (Re low, Im high)
-  Mode1Row* rows = nullptr;   // [KG * 128]
-  int* kg_k = nullptr;        // [KG] component of each group
-  int2* colrows = nullptr;    // [M q], tensor t = j q + k -> (first global row, r1)
-  int4* rowsrc = nullptr;     // [KG * 128] (tensor, a, valid) for the build
-};
-
 void mode1_release(Mode1Cache* c) {
   if (!c) return;
-  if (c->A) cudaFree(c->A);
-  if (c->rows) cudaFree(c->rows);
-  if (c->kg_k) cudaFree(c->kg_k);
-  if (c->colrows) cudaFree(c->colrows);
-  if (c->rowsrc) cudaFree(c->rowsrc);
+  for (void* ptr : {(void*)c->A, (void*)c->rows, (void*)c->kg_k, (void*)c->colrows, (void*)c->rowsrc, (void*)c->Bf,
+                    (void*)c->Wc, (void*)c->ew, (void*)c->chunkinfo, (void*)c->jtab})
+    if (ptr) cudaFree(ptr);
   delete c;
 }
 
@@ -139,6 +116,7 @@ int build_mode1_cache(Handle& h, cudaStream_t st) {
   }
   auto* c = new Mode1Cache();
   c->KG = KG;
+  c->gbase = gbase;
   c->n1p = (h.n1 + 7) / 8 * 8;
   const size_t abytes = sizeof(uint32_t) * (size_t)KG * 2 * c->n1p * kM1Rows;
   cudaError_t e = cudaMalloc(&c->A, abytes);
@@ -271,18 +249,7 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
                : "memory");
 }
 
-// 16 columns of this thread's TMEM lane, without waiting (tmem_wait_ld completes all of them)
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 
 struct M1Params {
   const uint32_t* A;

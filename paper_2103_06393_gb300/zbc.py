@@ -405,7 +405,8 @@ def zbc_rmatvec_noalloc(h: Handle, Phi, Psi, stream=None):
 
 
 TUNE_VARIANTS = (
-    "fwd_simt6", "fwd_simt9", "fwd_tf32x3", "fwd_bf16x3", "fwd_tc2", "adj_simt6", "adj_simt9", "adj_mode1",
+    "fwd_simt6", "fwd_simt9", "fwd_tf32x3", "fwd_bf16x3", "fwd_tc2", "fwd_mode1",
+    "adj_simt6", "adj_simt9", "adj_mode1",
 )
 
 
