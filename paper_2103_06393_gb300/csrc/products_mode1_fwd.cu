@@ -24,11 +24,11 @@
 // round-to-nearest ("folds"), two D buffers alternating, so K = 2 x (rows of component k) never
 // accumulates in one tensor-core sum.
 //
-// Per call: m1f_x_kernel (ex and the scaled X^T of each pass), then rmatvec's counterpart
-// matvec_mode1_kernel, persistent over items (component, pass, block of 128 (i23, s) rows):
+// Per call: m1f_x_kernel (ex and the scaled X^T of each pass), m1f_xe_kernel (X per chunk row),
+// then matvec_mode1_kernel, persistent over items (component, pass, block of 128 (i23, s) rows):
 //   copy warp  : per chunk of 32 rows, cp.async.bulk of U1's operand block (both terms), the W
-//                block of the item's i23 values, the X rows of the chunk's columns and the
-//                chunk's row -> column table into a stage ring
+//                block of the item's i23 values and the X values of the chunk's rows into a
+//                stage ring
 //   MMA warp   : per chunk 12 MMAs (4 K steps x 3 products), A from TMEM (two buffers), B from
 //                the stage, D in TMEM (two buffers of N = 2 n1f columns, n1f = n1 rounded up to 16)
 //   8 warps    : generate A (each warpgroup half of a chunk's rows), fold D into registers (each
@@ -230,6 +230,22 @@ __global__ void __launch_bounds__(256) m1f_x_kernel(const float2* __restrict__ X
   }
 }
 
+// XE[sc][c][r][s] = XT[sc][column of row r of chunk c][s]: each chunk row's X values, so that the
+// generator reads them without an index lookup (padding rows repeat a column; their W is zero)
+__global__ void __launch_bounds__(256) m1f_xe_kernel(const float2* __restrict__ XT, const int2* __restrict__ chunkinfo,
+                                                     const int8_t* __restrict__ jtab, int M, int NC, int P, int nsc,
+                                                     float2* __restrict__ XE) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nsc * NC * kFwdChunk * P) return;
+  const int s = (int)(e % P);
+  const int64_t t = e / P;
+  const int r = (int)(t % kFwdChunk);
+  const int64_t t2 = t / kFwdChunk;
+  const int c = (int)(t2 % NC), sc = (int)(t2 / NC);
+  const int j = chunkinfo[c].x + jtab[(int64_t)c * kFwdChunk + r];
+  XE[e] = XT[((int64_t)sc * M + j) * P + s];
+}
+
 // ---------------------------------------------------------------------------------------------
 // the product kernel
 // ---------------------------------------------------------------------------------------------
@@ -238,16 +254,14 @@ struct FwdParams {
   const uint32_t* Bf;
   const float2* Wc;
   const int* ew;
-  const int2* chunkinfo;
-  const int8_t* jtab;
-  const float2* XT;   // [nsc][M][P], scaled by 2^-ex
+  const float2* XE;   // [nsc][chunk][32][P]: X (scaled by 2^-ex) of each chunk row
   const int* ex;      // [nsc P]
   const int* chbase;  // [q + 1]
   float2* Y;
   int64_t ldy, nv;
   int* err;
-  int M, p, n1, n1f, n23, n23p, nsc, nblk, S;
-  uint32_t b_bytes, w_off, x_off, j_off, stage_bytes;
+  int NC, p, n1, n1f, n23, n23p, nsc, nblk, S;
+  uint32_t b_bytes, w_off, x_off, stage_bytes;
   int64_t nitems;  // q nsc nblk
 };
 
@@ -313,15 +327,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
             abort_flag = 1;
             break;
           }
-          const int2 ci = prm.chunkinfo[c];
-          const uint32_t xb = (uint32_t)ci.y * P * 8;
+          constexpr uint32_t wb = I * kFwdChunk * 8, xb = kFwdChunk * P * 8;
           unsigned char* sb = stages + (size_t)st * prm.stage_bytes;
-          mbar_arrive_expect_tx(&sfull[st], prm.b_bytes + (uint32_t)(I * kFwdChunk * 8) + xb + kFwdChunk);
+          mbar_arrive_expect_tx(&sfull[st], prm.b_bytes + wb + xb);
           bulk_g2s(sb, prm.Bf + (int64_t)c * (prm.b_bytes / 4), prm.b_bytes, &sfull[st]);
-          bulk_g2s(sb + prm.w_off, prm.Wc + ((int64_t)c * prm.n23p + (int64_t)blk * I) * kFwdChunk,
-                   (uint32_t)(I * kFwdChunk * 8), &sfull[st]);
-          bulk_g2s(sb + prm.x_off, prm.XT + ((int64_t)sc * prm.M + ci.x) * P, xb, &sfull[st]);
-          bulk_g2s(sb + prm.j_off, prm.jtab + (int64_t)c * kFwdChunk, kFwdChunk, &sfull[st]);
+          bulk_g2s(sb + prm.w_off, prm.Wc + ((int64_t)c * prm.n23p + (int64_t)blk * I) * kFwdChunk, wb, &sfull[st]);
+          bulk_g2s(sb + prm.x_off, prm.XE + ((int64_t)sc * prm.NC + c) * kFwdChunk * P, xb, &sfull[st]);
         }
       }
       if (abort_flag)  // let the copies in flight land before the CTA exits
@@ -429,16 +440,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
           break;
         }
         const unsigned char* sb = stages + (size_t)st * prm.stage_bytes;
-        const float2* Ws = (const float2*)(sb + prm.w_off) + i23l * kFwdChunk;  // this row's i23
-        const float2* Xs = (const float2*)(sb + prm.x_off) + s;                // [column][P]
-        const int8_t* js = (const int8_t*)(sb + prm.j_off);
+        const float4* Ws = (const float4*)(sb + prm.w_off) + i23l * (kFwdChunk / 2);  // this row's i23
+        const float2* Xs = (const float2*)(sb + prm.x_off) + s;                      // [chunk row][P]
 #pragma unroll
         for (int r0 = 0; r0 < 16; r0 += 8) {
           uint32_t hi[8], lo[8];
+          float4 w4[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) w4[r] = Ws[(16 * g + r0) / 2 + r];
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int rl = 16 * g + r0 + r;
-            const float2 c = cmul(Ws[rl], Xs[js[rl] * P]);
+            const float2 wv = (r & 1) ? make_float2(w4[r / 2].z, w4[r / 2].w) : make_float2(w4[r / 2].x, w4[r / 2].y);
+            const float2 c = cmul(wv, Xs[rl * P]);
             const __half2 h2 = __floats2half2_rn(c.x, c.y);
             const float2 hf = __half22float2(h2);
             const __half2 l2 = __floats2half2_rn(c.x - hf.x, c.y - hf.y);
@@ -488,7 +502,6 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   constexpr int I = kM1Rows / P;
   const Mode1Cache& mc = *h.cache->mode1;
   FwdParams prm;
-  prm.M = h.M;
   prm.p = p;
   prm.n1 = h.n1;
   prm.n1f = (h.n1 + 15) / 16 * 16;
@@ -503,8 +516,7 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   prm.b_bytes = (uint32_t)(2 * N * 128);
   prm.w_off = prm.b_bytes;
   prm.x_off = prm.w_off + (uint32_t)(I * kFwdChunk * 8);
-  prm.j_off = prm.x_off + (uint32_t)(kFwdChunk * P * 8);
-  prm.stage_bytes = (prm.j_off + 128 + 1023) / 1024 * 1024;
+  prm.stage_bytes = (prm.x_off + (uint32_t)(kFwdChunk * P * 8) + 1023) / 1024 * 1024;
   const size_t budget = 226 * 1024;
   prm.S = (int)std::min<size_t>(kM1MaxStages, (budget - 1024) / prm.stage_bytes);
   if (prm.S < 2) {
@@ -512,22 +524,24 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
     return ZBC_EINVAL;
   }
   const size_t smem = 1024 + (size_t)prm.S * prm.stage_bytes;
-  // scaled X^T per pass and the exponents; the chunk table on the device
-  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (size_t)prm.nsc * h.M * P + sizeof(int) * (size_t)prm.nsc * P +
-                           sizeof(int) * (h.q + 1) + 256));
+  // scaled X^T per pass, its expansion per chunk row, the exponents; the chunk table on the device
+  prm.NC = mc.chbase[h.q];
+  const size_t xt_elems = (size_t)prm.nsc * h.M * P, xe_elems = (size_t)prm.nsc * prm.NC * kFwdChunk * P;
+  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (xt_elems + xe_elems) + sizeof(int) * ((size_t)prm.nsc * P + h.q + 1)));
   float2* XT = (float2*)h.work_xt.ptr;
-  int* ex = (int*)(XT + (size_t)prm.nsc * h.M * P);
+  float2* XE = XT + xt_elems;
+  int* ex = (int*)(XE + xe_elems);
   int* chb = ex + prm.nsc * P;
   ZBC_TRY_CUDA(cudaMemcpyAsync(chb, mc.chbase.data(), sizeof(int) * (h.q + 1), cudaMemcpyHostToDevice, st));
   m1f_x_kernel<<<prm.nsc * P, 256, 0, st>>>(X, ldx, h.M, p, P, XT, ex);
+  m1f_xe_kernel<<<ceil_div((int64_t)xe_elems, 256), 256, 0, st>>>(XT, mc.chunkinfo, mc.jtab, h.M, prm.NC, P, prm.nsc,
+                                                                   XE);
   ZBC_TRY_CUDA(cudaGetLastError());
-  count_launch();
+  count_launch(2);
   prm.Bf = mc.Bf;
   prm.Wc = mc.Wc;
   prm.ew = mc.ew;
-  prm.chunkinfo = mc.chunkinfo;
-  prm.jtab = mc.jtab;
-  prm.XT = XT;
+  prm.XE = XE;
   prm.ex = ex;
   prm.chbase = chb;
   prm.Y = Y;
