@@ -498,26 +498,37 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
   if (warp == 0) tc::tmem_dealloc(tbase, prm.tcols);
 }
 
-// Psi'[j, s] = sum over partial slots, components and ranks of (j, k); fixed order
-__global__ void __launch_bounds__(256) mode1_reduce_kernel(const float2* __restrict__ partial,
-                                                           const int2* __restrict__ colrows, int q, int M, int nslots,
+// Psi'[j, s] = sum over partial slots, components and ranks of (j, k).  One CTA per (column, 16
+// right-hand sides); its 8 parts take the slots in turn and are added in a fixed order, so the
+// result does not depend on scheduling.
+__global__ void __launch_bounds__(128) mode1_reduce_kernel(const float2* __restrict__ partial,
+                                                           const int2* __restrict__ colrows, int q, int nslots,
                                                            int64_t rows_all, int ppad, int p,
                                                            float2* __restrict__ out, int64_t ldo) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)M * p) return;
-  const int j = (int)(e / p), s = (int)(e % p);
+  const int j = blockIdx.x;
+  const int s = blockIdx.y * 16 + (threadIdx.x & 15), part = threadIdx.x >> 4;
+  __shared__ float2 red[8][16];
   float2 acc = make_float2(0.f, 0.f);
-  for (int sl = 0; sl < nslots; ++sl)
+  if (s < p)
     for (int k = 0; k < q; ++k) {
       const int2 cr = colrows[(int64_t)j * q + k];
-      const float2* src = partial + ((int64_t)sl * rows_all + cr.x) * ppad + s;
-      for (int a = 0; a < cr.y; ++a) {
-        const float2 v = src[(int64_t)a * ppad];
-        acc.x += v.x;
-        acc.y += v.y;
-      }
+      for (int a = 0; a < cr.y; ++a)
+        for (int sl = part; sl < nslots; sl += 8) {
+          const float2 v = partial[((int64_t)sl * rows_all + cr.x + a) * ppad + s];
+          acc.x += v.x;
+          acc.y += v.y;
+        }
     }
-  out[j + ldo * s] = acc;
+  red[part][threadIdx.x & 15] = acc;
+  __syncthreads();
+  if (part == 0 && s < p) {
+    float2 t = red[0][threadIdx.x];
+    for (int i = 1; i < 8; ++i) {
+      t.x += red[i][threadIdx.x].x;
+      t.y += red[i][threadIdx.x].y;
+    }
+    out[j + ldo * s] = t;
+  }
 }
 
 template <int P, int NB>
@@ -564,7 +575,7 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   G.KC = 32;
   G.chunk_u32 = (uint32_t)NB * G.KC;
   const size_t stage_bytes = 8 * (size_t)G.chunk_u32;
-  const size_t budget = 225 * 1024;  // 7 stages of 32 KB, 5 of 40 KB or 3 of 64 KB, and the alignment slack
+  const size_t budget = 225 * 1024;  // 3 stages of 64 KB (N blocks of 256 rows), and the alignment slack
   const int S = (int)std::min<size_t>(kM1MaxStages, (budget - 1024) / stage_bytes);
   if (S < 2) {
     set_error("mode-1 adjoint: stage layout does not fit shared memory");
@@ -634,8 +645,8 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
         : NB == 64  ? launch_mode1<P, 64>(prm, smem, budget, grid, st)
                     : launch_mode1<P, 32>(prm, smem, budget, grid, st);
   ZBC_TRY(s);
-  mode1_reduce_kernel<<<ceil_div((int64_t)h.M * p, 256), 256, 0, st>>>((const float2*)h.work_partial.ptr, mc.colrows,
-                                                                       h.q, h.M, nslots, rows_all, ppad, p, out, ldo);
+  mode1_reduce_kernel<<<dim3(h.M, ceil_div(p, 16)), 128, 0, st>>>((const float2*)h.work_partial.ptr, mc.colrows, h.q,
+                                                                  nslots, rows_all, ppad, p, out, ldo);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return ZBC_OK;
