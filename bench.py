@@ -584,10 +584,11 @@ def run_batching(args):
             pair()
         ms = statistics.median(time_steps(pair, 5, lambda: flush.fill_(1), torch, stream))
         fv = min((k for k in tune if k.startswith("fwd_")), key=lambda k: tune[k])
-        per_p[str(p)] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "forward": fv,
-                         "fwd_ms": tune[fv], "adj_ms": min(tune["adj_simt6"], tune["adj_simt9"])}
+        av = min((k for k in tune if k.startswith("adj_")), key=lambda k: tune[k])
+        per_p[str(p)] = {"ms": ms, "tflops": F / (ms * 1e-3) / 1e12, "forward": fv, "adjoint": av,
+                         "fwd_ms": tune[fv], "adj_ms": tune[av]}
         bufs.append(pair)
-        log(f"[bench] batching p={p}: {ms:.3f} ms ({per_p[str(p)]['tflops']:.1f} TFLOP/s, {fv})")
+        log(f"[bench] batching p={p}: {ms:.3f} ms ({per_p[str(p)]['tflops']:.1f} TFLOP/s, {fv}, {av})")
 
     def mixed():
         for f in bufs:

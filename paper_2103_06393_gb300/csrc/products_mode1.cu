@@ -279,10 +279,10 @@ __device__ __forceinline__ void m1_item(const M1Params& prm, int64_t it, int& sc
 }
 
 // Shape of the main kernel for NB rows per N block: two D buffers while they fit beside A in
-// tensor memory (NB <= 160 for n1 <= 96), else one 256-column buffer drained by two epilogue
+// tensor memory (NB <= 160), else one buffer of 192 or 256 columns drained by two epilogue
 // warpgroups at once (each takes half of its columns), so that it is handed back after a single
-// round of TMEM loads.  Fewer, larger MMAs are what matters: the MMA issue costs about the same
-// per instruction for 128 and 160 columns.
+// round of TMEM loads.  Fewer, larger MMAs are what matters: an MMA costs at least ~95 cycles
+// to issue whatever its N.
 template <int NB>
 struct M1Shape {
   static constexpr int DB = NB > 160 ? 1 : 2;       // D buffers
@@ -542,10 +542,11 @@ static int launch_mode1(const M1Params& prm, size_t smem, size_t budget, int gri
 }
 
 // rows per N block for P right-hand sides per pass and A of 2 n1p TMEM columns: the widest MMA
-// that fits (256 columns, one D buffer; else 160 or a power of two, two D buffers), at most 16
-// values of i23 per block (the epilogue's W registers)
+// that fits (256 or 192 columns with one D buffer; else 160 or a power of two with two), at most
+// 16 values of i23 per block (the epilogue's W registers)
 static int mode1_nb(int P, int n1p) {
   if (P >= 8 && 256 + 2 * n1p <= 512) return 256;
+  if (P >= 8 && 192 + 2 * n1p <= 512) return 192;  // one buffer beside a wide A (n1 up to 160)
   if (P >= 8 && 2 * 160 + 2 * n1p <= 512) return 160;
   int NB = std::min(128, 32 * P);
   while (NB > 32 && 2 * NB + 2 * n1p > 512) NB /= 2;
@@ -640,6 +641,7 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
                    : launch_mode1<P, 32>(prm, smem, budget, grid, st);
   else
     s = NB == 256   ? launch_mode1<P, 256>(prm, smem, budget, grid, st)
+        : NB == 192 ? launch_mode1<P, 192>(prm, smem, budget, grid, st)
         : NB == 160 ? launch_mode1<P, 160>(prm, smem, budget, grid, st)
         : NB == 128 ? launch_mode1<P, 128>(prm, smem, budget, grid, st)
         : NB == 64  ? launch_mode1<P, 64>(prm, smem, budget, grid, st)

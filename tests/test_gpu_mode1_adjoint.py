@@ -171,6 +171,16 @@ def test_mode1_mixed_column_scales():
     assert rel_cols(zbc.from_colmajor(Psi), Po).max() < RTOL
 
 
+@pytest.mark.parametrize("p", [8, 16])
+def test_mode1_n1_160_single_buffer(p):
+    # n1 = 160: A takes 320 TMEM columns, so N blocks of 192 rows with one D buffer
+    n = (160, 6, 5)
+    w = inputs.scaled_workload("precision", n, m=4)
+    h, tens = _handle(w, 1e-5)
+    P, Po = _adj(h, n, tens, p, seed=19)
+    assert rel_cols(P, Po).max() < RTOL
+
+
 def test_mode1_wide_n1_and_limit():
     n = (200, 5, 3)   # n1 = 200: A takes 400 TMEM columns, N blocks of 32 rows
     w = inputs.scaled_workload("precision", n, m=3)
