@@ -30,7 +30,7 @@
 //                block of the item's i23 values and the X values of the chunk's rows into a
 //                stage ring
 //   MMA warp   : per chunk 12 MMAs (4 K steps x 3 products), A from TMEM (two buffers), B from
-//                the stage, D in TMEM (two buffers of N = 2 n1f columns, n1f = n1 rounded up to 16)
+//                the stage, D in TMEM (two buffers of N = 2 n1t columns for an i1 tile of n1t rows)
 //   8 warps    : generate A (each warpgroup half of a chunk's rows), fold D into registers (each
 //                warpgroup half of D's columns) and write Y.
 #include "mode1.cuh"
@@ -39,7 +39,14 @@ namespace zbc {
 
 constexpr int kFwdChunk = 32;   // rows (j, a) per K chunk
 constexpr int kFwdSeg = 3;      // chunks per tensor-core accumulation
-constexpr int kFwdMaxN1p = 96;  // n1f limit: two D buffers of 2 n1f columns + two A buffers of 64 in TMEM
+constexpr int kFwdMaxN1p = 96;  // i1 tile limit: two D buffers of 2 n1t columns + two A buffers of 64 in TMEM
+
+// i1 tiles of the forward: ntile1 = ceil(n1 / 96) tiles of n1t rows (a multiple of 16), each an
+// item dimension of its own (the W X operand is generated once per tile, which is cheap)
+static void fwd_tiles(int n1, int& ntile1, int& n1t) {
+  ntile1 = (n1 + kFwdMaxN1p - 1) / kFwdMaxN1p;
+  n1t = ((n1 + ntile1 - 1) / ntile1 + 15) / 16 * 16;
+}
 constexpr int kFwdThreads = 32 * 10;
 
 // ---------------------------------------------------------------------------------------------
@@ -88,18 +95,18 @@ __global__ void __launch_bounds__(256) m1f_wc_kernel(const float2* __restrict__ 
   Wc[((int64_t)c * n23p + i23) * kFwdChunk + rl] = v;
 }
 
-// U1's operand blocks: chunk c, term t, row n = 2 i1 + e (N = 2 n1f rows), 16-byte piece kc of
-// rows 4 kc .. 4 kc + 3 of the chunk, in the 128-byte swizzled K-major layout
+// U1's operand blocks: chunk c, i1 tile t1, term t, row n = 2 (i1 - t1 n1t) + e (N = 2 n1t rows),
+// 16-byte piece kc of rows 4 kc .. 4 kc + 3 of the chunk, in the 128-byte swizzled K-major layout
 __global__ void __launch_bounds__(256) m1f_b_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc,
                                                     const int4* __restrict__ rowsrc, const Mode1Row* __restrict__ rows,
                                                     const int* __restrict__ chunk_row0, const int* __restrict__ chunk_nr,
-                                                    int n1, int n1f, uint32_t* __restrict__ Bf) {
-  const int c = blockIdx.y;
-  const int N = 2 * n1f;
+                                                    int n1, int n1t, uint32_t* __restrict__ Bf) {
+  const int c = blockIdx.y, t1 = blockIdx.z, ntile1 = gridDim.z;
+  const int N = 2 * n1t;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (row n, piece kc)
   if (e >= N * 8) return;
   const int n = e / 8, kc = e % 8;
-  const int i1 = n >> 1, eo = n & 1;
+  const int i1 = t1 * n1t + (n >> 1), eo = n & 1;
   uint32_t hw[4], lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(256) m1f_b_kernel(const float2* __restrict__ p
     lw[i] = *reinterpret_cast<const uint32_t*>(&vl);
   }
   const int64_t term = (int64_t)N * kFwdChunk;  // 32-bit words per term
-  uint32_t* blk = Bf + (int64_t)c * 2 * term + tc::sw128_off(n, kc) / 4;
+  uint32_t* blk = Bf + ((int64_t)c * ntile1 + t1) * 2 * term + tc::sw128_off(n, kc) / 4;
   *reinterpret_cast<uint4*>(blk) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
   *reinterpret_cast<uint4*>(blk + term) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
@@ -131,7 +138,7 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   Mode1Cache& mc = *h.cache->mode1;
   if (mc.fwd) return ZBC_OK;
   const int q = h.q, M = h.M;
-  const int n23 = h.n2 * h.n3, n23p = (n23 + 15) / 16 * 16;
+  const int n23 = h.n2 * h.n3, n23p = (n23 + 31) / 32 * 32;  // whole blocks of up to 32 i23
   // chunks of 32 rows per component; per chunk its first row (global), rows, component, first
   // column and columns, and each row's column relative to the first
   std::vector<int> chbase(q + 1, 0), nrows(q, 0);
@@ -156,8 +163,10 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
     }
   }
   const int NC = chbase[q];
-  const int N = 2 * ((h.n1 + 15) / 16 * 16);  // rows 2 i1 + e, i1 < n1 rounded up to 16
-  const size_t bwords = (size_t)NC * 2 * N * kFwdChunk;
+  int ntile1, n1t;
+  fwd_tiles(h.n1, ntile1, n1t);
+  const int N = 2 * n1t;  // rows 2 i1 + e of one i1 tile
+  const size_t bwords = (size_t)NC * ntile1 * 2 * N * kFwdChunk;
   const size_t wc_elems = (size_t)NC * n23p * kFwdChunk;
   int *d_row0 = nullptr, *d_nr = nullptr, *d_ck = nullptr, *d_gbase = nullptr, *d_nrows = nullptr;
   cudaError_t e = cudaMalloc(&mc.Bf, sizeof(uint32_t) * bwords);
@@ -185,8 +194,8 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
                                                                mc.ew);
     m1f_wc_kernel<<<dim3(ceil_div((int64_t)n23p * kFwdChunk, 256), NC), 256, 0, st>>>(
         h.cache->data, mc.rows, d_row0, d_ck, d_nr, mc.ew, n23, n23p, mc.Wc);
-    m1f_b_kernel<<<dim3(ceil_div(N * 8, 256), NC), 256, 0, st>>>(h.d_pool, h.d_desc, mc.rowsrc, mc.rows, d_row0, d_nr,
-                                                                h.n1, N / 2, mc.Bf);
+    m1f_b_kernel<<<dim3(ceil_div(N * 8, 256), NC, ntile1), 256, 0, st>>>(h.d_pool, h.d_desc, mc.rowsrc, mc.rows,
+                                                                        d_row0, d_nr, h.n1, n1t, mc.Bf);
     count_launch(3);
     e = cudaGetLastError();
   }
@@ -260,18 +269,20 @@ struct FwdParams {
   float2* Y;
   int64_t ldy, nv;
   int* err;
-  int NC, p, n1, n1f, n23, n23p, nsc, nblk, S;
+  int NC, p, n1, n1t, ntile1, n23, n23p, nsc, nblk, S;
   uint32_t b_bytes, w_off, x_off, stage_bytes;
-  int64_t nitems;  // q nsc nblk
+  int64_t nitems;  // q ntile1 nsc nblk
 };
 
-// item -> (component k, pass sc, block of I values of i23); blocks vary fastest, so the CTAs
-// running at one time stream the same component's U1 blocks (from L2)
-__device__ __forceinline__ void m1f_item(const FwdParams& prm, int64_t it, int& k, int& sc, int& blk) {
+// item -> (component k, i1 tile t1, pass sc, block of I values of i23); blocks vary fastest, so
+// the CTAs running at one time stream the same U1 blocks (from L2)
+__device__ __forceinline__ void m1f_item(const FwdParams& prm, int64_t it, int& k, int& t1, int& sc, int& blk) {
   blk = (int)(it % prm.nblk);
-  const int64_t t = it / prm.nblk;
+  int64_t t = it / prm.nblk;
   sc = (int)(t % prm.nsc);
-  k = (int)(t / prm.nsc);
+  t /= prm.nsc;
+  t1 = (int)(t % prm.ntile1);
+  k = (int)(t / prm.ntile1);
 }
 
 // 8 consecutive 32-bit columns of this thread's TMEM lane
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
   __shared__ volatile int abort_flag;
   unsigned char* stages = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = prm.S;
-  const int N = 2 * prm.n1f;  // D columns: (i1, Re / Im)
+  const int N = 2 * prm.n1t;  // D columns: (i1 of the tile, Re / Im)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   if (warp == 0) tc::tmem_alloc(&tbase, 512);
@@ -318,8 +329,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
     if (lane == 0) {
       uint32_t cnt = 0;
       for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x) {
-        int k, sc, blk;
-        m1f_item(prm, it, k, sc, blk);
+        int k, t1, sc, blk;
+        m1f_item(prm, it, k, t1, sc, blk);
         const int c1 = prm.chbase[k + 1];
         for (int c = prm.chbase[k]; c < c1 && !abort_flag; ++c, ++cnt) {
           const int st = cnt % S;
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
           constexpr uint32_t wb = I * kFwdChunk * 8, xb = kFwdChunk * P * 8;
           unsigned char* sb = stages + (size_t)st * prm.stage_bytes;
           mbar_arrive_expect_tx(&sfull[st], prm.b_bytes + wb + xb);
-          bulk_g2s(sb, prm.Bf + (int64_t)c * (prm.b_bytes / 4), prm.b_bytes, &sfull[st]);
+          bulk_g2s(sb, prm.Bf + ((int64_t)c * prm.ntile1 + t1) * (prm.b_bytes / 4), prm.b_bytes, &sfull[st]);
           bulk_g2s(sb + prm.w_off, prm.Wc + ((int64_t)c * prm.n23p + (int64_t)blk * I) * kFwdChunk, wb, &sfull[st]);
           bulk_g2s(sb + prm.x_off, prm.XE + ((int64_t)sc * prm.NC + c) * kFwdChunk * P, xb, &sfull[st]);
         }
@@ -346,8 +357,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
       const uint32_t bterm = prm.b_bytes / 2;
       uint32_t gc = 0, gs = 0;
       for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x) {
-        int k, sc, blk;
-        m1f_item(prm, it, k, sc, blk);
+        int k, t1, sc, blk;
+        m1f_item(prm, it, k, t1, sc, blk);
         const int nch = prm.chbase[k + 1] - prm.chbase[k];
         for (int cl = 0; cl < nch && !abort_flag; ++cl, ++gc) {
           const bool first = cl % kFwdSeg == 0, last = cl % kFwdSeg == kFwdSeg - 1 || cl == nch - 1;
@@ -386,15 +397,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
     const int row = (warp & 3) * 32 + lane;        // TMEM lane = (i23l, s)
     const uint32_t lanebase = (uint32_t)((warp & 3) * 32) << 16;
     const int i23l = row / P, s = row % P;
-    const int H = prm.n1f;                         // D columns per warpgroup
+    const int H = prm.n1t;                         // D columns per warpgroup
     float acc[kFwdMaxN1p];
 #pragma unroll
     for (int i = 0; i < kFwdMaxN1p; ++i) acc[i] = 0.f;
     uint32_t gc = 0, gs = 0;
     for (int64_t it = blockIdx.x; it < prm.nitems; it += gridDim.x) {
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-      int k, sc, blk;
-      m1f_item(prm, it, k, sc, blk);
+      int k, t1, sc, blk;
+      m1f_item(prm, it, k, t1, sc, blk);
       const int nch = prm.chbase[k + 1] - prm.chbase[k];
       const int nseg = (nch + kFwdSeg - 1) / kFwdSeg;
       const uint32_t gs0 = gs;
@@ -476,14 +487,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
         if (lane == 0) abort_flag = 1;
         break;
       }
-      // Y rows i1 in [g H / 2, g H / 2 + H / 2) of voxel column i23 for right-hand side s
+      // Y rows i1 in t1 n1t + [g H / 2, g H / 2 + H / 2) of voxel column i23 for right-hand side s
       const int i23 = blk * I + i23l, sg = sc * P + s;
       if (i23 < prm.n23 && sg < prm.p) {
         const float f = ldexpf(1.f, prm.ew[(int64_t)k * prm.n23p + i23] + prm.ex[sg] - kHalfShift);
         float2* y = prm.Y + (int64_t)k * prm.nv + (int64_t)prm.n1 * i23 + prm.ldy * sg;
 #pragma unroll
         for (int ii = 0; ii < kFwdMaxN1p / 2; ++ii) {
-          const int i1 = g * (H / 2) + ii;
+          const int i1 = t1 * prm.n1t + g * (H / 2) + ii;
           if (ii < H / 2 && i1 < prm.n1) y[i1] = make_float2(acc[2 * ii] * f, acc[2 * ii + 1] * f);
         }
       }
@@ -504,15 +515,15 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   FwdParams prm;
   prm.p = p;
   prm.n1 = h.n1;
-  prm.n1f = (h.n1 + 15) / 16 * 16;
+  fwd_tiles(h.n1, prm.ntile1, prm.n1t);
   prm.n23 = h.n2 * h.n3;
   prm.n23p = mc.n23p;
   prm.nsc = ceil_div(p, P);
   prm.nblk = mc.n23p / I;
-  prm.nitems = (int64_t)h.q * prm.nsc * prm.nblk;
+  prm.nitems = (int64_t)h.q * prm.ntile1 * prm.nsc * prm.nblk;
   prm.ldy = ldy;
   prm.nv = h.nv();
-  const int N = 2 * prm.n1f;
+  const int N = 2 * prm.n1t;
   prm.b_bytes = (uint32_t)(2 * N * 128);
   prm.w_off = prm.b_bytes;
   prm.x_off = prm.w_off + (uint32_t)(I * kFwdChunk * 8);
@@ -554,18 +565,12 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   return ZBC_OK;
 }
 
-// Y = Z X on the handle's stored columns (X has M rows), mode-1 tensor-core form; p <= 16 per
-// pass, n1 <= 96
+// Y = Z X on the handle's stored columns (X has M rows), mode-1 tensor-core form: passes of 4, 8
+// or 16 right-hand sides (a block of 128 rows holds 32, 16 or 8 values of i23), i1 tiles of at
+// most 96
 int matvec_mode1(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st) {
-  if ((h.n1 + 15) / 16 * 16 > kFwdMaxN1p) {
-    set_error("mode-1 forward: n1 = %d does not fit tensor memory (n1 <= %d)", h.n1, kFwdMaxN1p);
-    return ZBC_EINVAL;
-  }
-  if (p < 5) {
-    set_error("mode-1 forward: needs p >= 5 right-hand sides (a block of 128 rows holds 16 or 8 per i23)");
-    return ZBC_EINVAL;
-  }
   ZBC_TRY(build_mode1_fwd(h, st));
+  if (p <= 4) return matvec_mode1_p<4>(h, X, ldx, p, Y, ldy, st);
   if (p <= 8) return matvec_mode1_p<8>(h, X, ldx, p, Y, ldy, st);
   return matvec_mode1_p<kM1MaxP>(h, X, ldx, p, Y, ldy, st);
 }

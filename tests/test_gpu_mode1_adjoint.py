@@ -197,7 +197,7 @@ def test_mode1_wide_n1_and_limit():
     assert e.value.status == zbc.ZBC_EINVAL
 
 
-def test_mode1_repeatable_and_small_p_forward_rejected():
+def test_mode1_repeatable():
     w = inputs.scaled_workload("precision", (24, 16, 12), m=8)
     h, tens = _handle(w, 1e-6)
     Phi = zbc.to_colmajor(inputs.cn01((3 * w.grid.nv, 16), seed=4).astype(np.complex64))
@@ -208,9 +208,3 @@ def test_mode1_repeatable_and_small_p_forward_rejected():
         zbc.zbc_product_status(h)
         outs.append(zbc.from_colmajor(Psi))
     assert np.array_equal(outs[0], outs[1])
-    # the forward's mode-1 form needs p >= 5 (a block of 128 rows holds 8 or 16 per i23)
-    X = zbc.colmajor(len(tens), 2, torch.complex64)
-    Y = zbc.colmajor(3 * w.grid.nv, 2, torch.complex64)
-    with pytest.raises(zbc.ZbcError) as e:
-        zbc.zbc_matvec(h, X, Y, zbc.TC_MODE1)
-    assert e.value.status == zbc.ZBC_EINVAL

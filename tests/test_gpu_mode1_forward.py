@@ -1,10 +1,10 @@
 """The forward product Y = Z X in its mode-1 tensor-core form (ZBC_TC_MODE1: per block of 128
 (i23, s) rows one fp16 hi/lo tcgen05 GEMM over the (column, rank) rows, A = W X generated on the
 CUDA cores into tensor memory, B = U1, the accumulator folded into FP32 registers every 3 chunks)
-against the FP64 oracle on the same compressed data: 8 and 16 right-hand sides per pass, several
-passes, ragged grids (n1 not a multiple of 16, i23 blocks cut by the end of n2 n3), chunks that
-hold one column or 32, ranks up to 64, ACA storage, extreme and mixed scales of X, the n1 and p
-limits, and bit-for-bit repeatability."""
+against the FP64 oracle on the same compressed data: 4, 8 and 16 right-hand sides per pass,
+several passes, ragged grids (n1 not a multiple of 16, i23 blocks cut by the end of n2 n3), i1
+tiles (n1 > 96), chunks that hold one column or 32, ranks up to 64, ACA storage, extreme and mixed
+scales of X, and bit-for-bit repeatability."""
 import numpy as np
 import pytest
 
@@ -72,7 +72,7 @@ def _fwd(h, shape, tens, p, seed=0, X=None, V=None, prec=None):
     return zbc.from_colmajor(Y), Yo
 
 
-@pytest.mark.parametrize("p", [5, 8, 9, 16, 17, 40])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 8, 9, 16, 17, 40])
 def test_mode1_fwd_tiny(p):
     w = inputs.workload("tiny")
     h, tens = _handle(w, 1e-8)
@@ -147,15 +147,17 @@ def test_mode1_fwd_mixed_column_scales():
     assert rel_cols(Y, Yo).max() < RTOL
 
 
-def test_mode1_fwd_limits_and_repeatable():
-    n = (100, 4, 3)   # n1 rounded up to 16 = 112 > 96: does not fit tensor memory
-    w = inputs.scaled_workload("precision", n, m=2)
+@pytest.mark.parametrize("n,p", [((100, 4, 3), 8), ((160, 6, 5), 16), ((200, 3, 2), 3), ((97, 5, 4), 16)])
+def test_mode1_fwd_i1_tiles(n, p):
+    # n1 > 96: i1 tiles of at most 96 rows (100 -> 2 x 64, 160 -> 2 x 80, 200 -> 3 x 80, 97 -> 2 x 64),
+    # the last tile partly past n1
+    w = inputs.scaled_workload("precision", n, m=4)
     h, tens = _handle(w, 1e-5)
-    X = zbc.colmajor(len(tens), 8, torch.complex64)
-    Y = zbc.colmajor(3 * int(np.prod(n)), 8, torch.complex64)
-    with pytest.raises(zbc.ZbcError) as e:
-        zbc.zbc_matvec(h, X, Y, zbc.TC_MODE1)
-    assert e.value.status == zbc.ZBC_EINVAL
+    Y, Yo = _fwd(h, n, tens, p, seed=23)
+    assert rel_cols(Y, Yo).max() < RTOL
+
+
+def test_mode1_fwd_repeatable():
     w = inputs.scaled_workload("precision", (24, 16, 12), m=8)
     h, tens = _handle(w, 1e-6)
     X = zbc.to_colmajor(inputs.cn01((len(tens), 16), seed=4).astype(np.complex64))
