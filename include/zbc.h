@@ -63,7 +63,8 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  * TC_MODE1  : the products regrouped so that the mode-1 product is a dense tcgen05 GEMM
  *             (fp16 hi+lo operands scaled by powers of two, 3 products, FP32 accumulation).
  *             Adjoint: T = U1^H Phi^k per group of 128 (column, rank) rows, then
- *             Psi_j = sum conj(W) T over (rank, i2, i3) on CUDA cores; needs n1 <= 224.
+ *             Psi_j = sum conj(W) T over (rank, i2, i3) on CUDA cores (i1 tiles of 160
+ *             beyond n1 = 224).
  *             Forward: per block of 128 (i2 i3, RHS) rows and i1 tile of at most 96,
  *             Y^k = U1 (W X) over all (column, rank) rows, W X generated on CUDA cores, the
  *             tensor-core sum folded into FP32 every 96 rows.

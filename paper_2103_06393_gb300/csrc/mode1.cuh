@@ -16,7 +16,7 @@ namespace zbc {
 constexpr int kM1Rows = 128;       // (column, rank) rows per group = MMA M = TMEM lanes
 constexpr int kM1MaxP = 16;        // right-hand sides per pass
 constexpr int kM1MaxStages = 8;
-constexpr int kM1MaxN1p = 224;     // A (2 n1p TMEM columns) + a D buffer of >= 32 columns
+constexpr int kM1MaxN1p = 224;     // widest A of the adjoint without i1 tiles (2 x 224 TMEM columns + D)
 
 struct Mode1Row {
   int64_t wbase;  // W_{kj}[i23 = 0, a] in the decompression cache; -1 for a padding row

@@ -154,6 +154,7 @@ struct M1Geo {
   int nsc;            // passes over the right-hand sides (ceil(p / P))
   int n23, NBT;       // n2 n3, N blocks per (component, pass)
   int n1, n1p, KC, nkc;
+  int nkt, ntile1;     // K chunks per i1 tile, i1 tiles (A of one tile sits in TMEM at a time)
   uint32_t chunk_u32;  // one term of one K chunk: NB * KC 32-bit words
   __host__ __device__ int64_t block_u32(int k, int sc, int nb, int c) const {
     return ((((int64_t)k * nsc + sc) * NBT + nb) * nkc + c) * 2 * chunk_u32;
@@ -258,20 +259,22 @@ struct M1Params {
   const float2* W;  // decompression cache
   const uint32_t* Bop;
   const int* Eblk;
-  float2* partial;  // [NR * EG slots][KG * 128][ppad]
+  float2* partial;  // [NR * ntile1 * EG slots][KG * 128][ppad]
   int* err;
   M1Geo G;
   int KG, NR, S, ppad;
   uint32_t tcols;   // allocated TMEM columns
-  int64_t nitems;   // nsc * NR * KG
+  int64_t nitems;   // nsc * NR * ntile1 * KG
 };
 
-// item -> (pass sc, N range nr, group kg); groups vary fastest, so the CTAs running at one time
-// share their N range and read the same B blocks (from L2)
-__device__ __forceinline__ void m1_item(const M1Params& prm, int64_t it, int& sc, int& nr, int& kg, int& nb0,
+// item -> (pass sc, N range nr, i1 tile t1, group kg); groups vary fastest, so the CTAs running
+// at one time share their N range and tile and read the same B blocks (from L2)
+__device__ __forceinline__ void m1_item(const M1Params& prm, int64_t it, int& sc, int& nr, int& t1, int& kg, int& nb0,
                                         int& nb1) {
   kg = (int)(it % prm.KG);
-  const int64_t t = it / prm.KG;
+  int64_t t = it / prm.KG;
+  t1 = (int)(t % prm.G.ntile1);
+  t /= prm.G.ntile1;
   nr = (int)(t % prm.NR);
   sc = (int)(t / prm.NR);
   nb0 = (int)((int64_t)prm.G.NBT * nr / prm.NR);
@@ -326,18 +329,20 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
   __syncthreads();
   tc::fence_after();
   const uint32_t tD = tbase;               // D buffers: columns [b NB, (b + 1) NB)
-  const uint32_t tA = tbase + DB * NB;     // A: hi in [DB NB, DB NB + n1p), lo after it
+  const uint32_t tAw = (uint32_t)G.nkt * G.KC;  // TMEM columns of one term of a tile's A
+  const uint32_t tA = tbase + DB * NB;          // A: hi in [DB NB, DB NB + tAw), lo after it
 
   if (warp == copy_warp) {
     // ---------------- copy warp: B blocks into the stage ring ----------------
     if (lane == 0) {
       uint32_t cnt = 0;
       for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x) {
-        int sc, nr, kg, nb0, nb1;
-        m1_item(prm, it, sc, nr, kg, nb0, nb1);
+        int sc, nr, t1, kg, nb0, nb1;
+        m1_item(prm, it, sc, nr, t1, kg, nb0, nb1);
+        const int c_lo = t1 * G.nkt, c_hi = min(G.nkc, c_lo + G.nkt);
         const int k = prm.kg_k[kg];
         for (int nb = nb0; nb < nb1 && !abort_flag; ++nb)
-          for (int c = 0; c < G.nkc; ++c, ++cnt) {
+          for (int c = c_lo; c < c_hi; ++c, ++cnt) {
             const int st = cnt % S;
             if (cnt >= (uint32_t)S && (abort_flag || !tc::mbar_wait(&sempty[st], ((cnt / S) - 1) & 1))) {
               abort_flag = 1;
@@ -358,8 +363,9 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
       const uint32_t idesc = tc::instr_desc(128, NB, 0);  // kind::f16, f16 operands, FP32 D
       uint32_t cnt = 0, dc = 0, ai = 0;
       for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x, ++ai) {
-        int sc, nr, kg, nb0, nb1;
-        m1_item(prm, it, sc, nr, kg, nb0, nb1);
+        int sc, nr, t1, kg, nb0, nb1;
+        m1_item(prm, it, sc, nr, t1, kg, nb0, nb1);
+        const int c_lo = t1 * G.nkt, c_hi = min(G.nkc, c_lo + G.nkt);
         if (!tc::mbar_wait(&afull, ai & 1)) {
           abort_flag = 1;
           break;
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
           }
           tc::fence_after();
           const uint32_t d = tD + buf * NB;
-          for (int c = 0; c < G.nkc; ++c, ++cnt) {
+          for (int c = c_lo; c < c_hi; ++c, ++cnt) {
             const int st = cnt % S;
             if (!tc::mbar_wait(&sfull[st], (cnt / S) & 1)) {
               abort_flag = 1;
@@ -382,14 +388,15 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
             }
             tc::fence_after();
             const int ksn = min(G.KC, G.n1p - c * G.KC) / 8;
+            const uint32_t cofs = (uint32_t)(c - c_lo) * G.KC;  // the chunk's first column in A
             const uint32_t sb = tc::smem_u32(stages + (size_t)st * stage_bytes);
             for (int ks = 0; ks < ksn; ++ks) {
-              const uint32_t acol = (uint32_t)(c * G.KC + 8 * ks);
+              const uint32_t acol = cofs + 8 * ks;
               const uint64_t bh = tc::smem_desc_sw128(sb + ks * 32);
               const uint64_t bl = tc::smem_desc_sw128(sb + 4u * G.chunk_u32 + ks * 32);
-              tc::mma_ts(d, tA + acol, bh, idesc, (c | ks) != 0);    // hi . hi
+              tc::mma_ts(d, tA + acol, bh, idesc, (c != c_lo || ks != 0) ? 1u : 0u);  // hi . hi
               tc::mma_ts(d, tA + acol, bl, idesc, 1u);               // hi . lo
-              tc::mma_ts(d, tA + G.n1p + acol, bh, idesc, 1u);       // lo . hi
+              tc::mma_ts(d, tA + tAw + acol, bh, idesc, 1u);         // lo . hi
             }
             tc::commit(&sempty[st]);
           }
@@ -407,23 +414,30 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
     uint32_t dc = 0;
     for (int64_t it = blockIdx.x; it < prm.nitems; it += gridDim.x) {
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-      int sc, nr, kg, nb0, nb1;
-      m1_item(prm, it, sc, nr, kg, nb0, nb1);
+      int sc, nr, t1, kg, nb0, nb1;
+      m1_item(prm, it, sc, nr, t1, kg, nb0, nb1);
       const int k = prm.kg_k[kg];
-      // A of group kg, the warpgroups splitting its columns; the previous item's MMAs are complete
-      // (its last D fill was drained, and that fill's commit came after all of them)
+      // A of group kg on the item's i1 tile, the warpgroups splitting its columns; the previous
+      // item's MMAs are complete (its last D fill was drained, and that fill's commit came after
+      // all of them)
       {
+        const int i_lo = t1 * G.nkt * G.KC, i_hi = min(G.n1p, i_lo + G.nkt * G.KC);
+        const int nloc = (i_hi - i_lo) / 4;  // 4-column blocks per term
         const uint4* src = reinterpret_cast<const uint4*>(prm.A) + (int64_t)kg * 2 * (G.n1p / 4) * kM1Rows + l;
-        const int ncb = 2 * (G.n1p / 4);
+        const int ncb = 2 * nloc;
         const int cb_lo = ncb * eg / EG, cb_hi = ncb * (eg + 1) / EG;
         for (int cb0 = cb_lo; cb0 < cb_hi; cb0 += 8) {  // 8 loads in flight, then their stores
           uint4 v[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (cb0 + i < cb_hi) v[i] = __ldg(src + (int64_t)(cb0 + i) * kM1Rows);
+          for (int i = 0; i < 8; ++i) {
+            const int cb = cb0 + i, term = cb >= nloc, loc = cb - term * nloc;
+            if (cb < cb_hi) v[i] = __ldg(src + ((int64_t)term * (G.n1p / 4) + i_lo / 4 + loc) * kM1Rows);
+          }
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (cb0 + i < cb_hi) tmem_st4(tA + lanebase + 4 * (cb0 + i), v[i]);
+          for (int i = 0; i < 8; ++i) {
+            const int cb = cb0 + i, term = cb >= nloc, loc = cb - term * nloc;
+            if (cb < cb_hi) tmem_st4(tA + lanebase + term * tAw + 4 * loc, v[i]);
+          }
         }
         tc::tmem_wait_st();
         tc::fence_before();
@@ -486,8 +500,8 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
         }
       }
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-      float2* out = prm.partial +
-                    ((int64_t)(nr * EG + eg) * prm.KG * kM1Rows + (int64_t)kg * kM1Rows + l) * prm.ppad + sc * P;
+      float2* out = prm.partial + ((int64_t)((nr * G.ntile1 + t1) * EG + eg) * prm.KG * kM1Rows +
+                                   (int64_t)kg * kM1Rows + l) * prm.ppad + sc * P;
 #pragma unroll
       for (int s = 0; s < P; ++s) out[s] = acc[s];
     }
@@ -563,17 +577,22 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   G.n1p = mc.n1p;
   G.n23 = h.n2 * h.n3;
   G.nsc = ceil_div(p, P);
-  const int NB = mode1_nb(P, G.n1p);
+  G.KC = 32;
+  G.nkc = ceil_div(G.n1p, 32);
+  // i1 tiles: A of the whole n1 while it fits beside a D buffer (n1 <= 224), else tiles of 5 K
+  // chunks (160 i1, beside one 192-column D buffer); each tile's partial sums get their own slots
+  G.nkt = G.n1p <= kM1MaxN1p ? G.nkc : 5;
+  G.ntile1 = ceil_div(G.nkc, G.nkt);
+  const int tAw = G.nkt * G.KC;  // TMEM columns per term of a tile's A (whole K chunks)
+  const int NB = mode1_nb(P, tAw);
   const int DB = NB > 160 ? 1 : 2, EG = NB > 160 ? 2 : 1;
-  if (NB < 2 * P || DB * NB + 2 * G.n1p > 512) {
-    set_error("mode-1 adjoint: n1 = %d does not fit tensor memory (n1 <= %d)", h.n1, kM1MaxN1p);
+  if (NB < 2 * P || DB * NB + 2 * tAw > 512) {
+    set_error("mode-1 adjoint: %d right-hand sides per pass do not fit tensor memory beside A", P);
     return ZBC_EINVAL;
   }
   G.NB = NB;
   G.I = NB / (2 * P);
   G.NBT = ceil_div(G.n23, G.I);
-  G.nkc = ceil_div(G.n1p, 32);
-  G.KC = 32;
   G.chunk_u32 = (uint32_t)NB * G.KC;
   const size_t stage_bytes = 8 * (size_t)G.chunk_u32;
   const size_t budget = 225 * 1024;  // 3 stages of 64 KB (N blocks of 256 rows), and the alignment slack
@@ -583,13 +602,13 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
     return ZBC_EINVAL;
   }
   const size_t smem = 1024 + (size_t)S * stage_bytes;
-  // items: N ranges x groups per pass, balanced over one CTA per SM; an item's cost is its
-  // N blocks plus about two for loading A and writing its partial sums
+  // items: N ranges x i1 tiles x groups per pass, balanced over one CTA per SM; an item's cost is
+  // its N blocks plus about two for loading A and writing its partial sums
   const int nsm = sm_count();
   int NR = 1;
   double best = 1e300;
   for (int r = 1; r <= std::min(G.NBT, 64); ++r) {
-    const int64_t items = (int64_t)G.nsc * r * mc.KG;
+    const int64_t items = (int64_t)G.nsc * r * G.ntile1 * mc.KG;
     const int64_t per = (items + nsm - 1) / nsm;
     const double cost = (double)per * ((double)G.NBT / r + 2.0);
     if (cost < best * 0.999) {
@@ -597,7 +616,7 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
       NR = r;
     }
   }
-  const int64_t nitems = (int64_t)G.nsc * NR * mc.KG;
+  const int64_t nitems = (int64_t)G.nsc * NR * G.ntile1 * mc.KG;
   const int grid = (int)std::min<int64_t>(nsm, nitems);
   // workspaces: B operand blocks + exponents; partial sums (one slot per N range and warpgroup)
   const size_t bop_bytes = 4 * (size_t)h.q * G.nsc * G.NBT * G.nkc * 2 * G.chunk_u32;
@@ -605,7 +624,7 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   ZBC_TRY(h.work_phi.ensure(bop_bytes + e_bytes));
   const int ppad = G.nsc * P;
   const int64_t rows_all = (int64_t)mc.KG * kM1Rows;
-  const int nslots = NR * EG;
+  const int nslots = NR * G.ntile1 * EG;
   ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)nslots * rows_all * ppad));
   uint32_t* Bop = (uint32_t*)h.work_phi.ptr;
   int* Eblk = (int*)((unsigned char*)h.work_phi.ptr + bop_bytes);
@@ -627,7 +646,7 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   prm.S = S;
   prm.ppad = ppad;
   uint32_t tcols = 32;
-  while (tcols < (uint32_t)(DB * NB + 2 * G.n1p)) tcols <<= 1;
+  while (tcols < (uint32_t)(DB * NB + 2 * tAw)) tcols <<= 1;
   prm.tcols = tcols;
   prm.nitems = nitems;
   int s;

@@ -2,8 +2,8 @@
 one fp16 hi/lo tcgen05 GEMM per group of 128 (column, rank) rows, then sum conj(W) T) against the
 FP64 oracle on the same compressed data: right-hand-side counts that pad the pass or need several
 passes, ragged grids (n1 not a multiple of 8, N blocks cut by the end of i23), groups that split a
-column's ranks, ranks up to 64, many columns, ACA storage, extreme scales of Phi, the n1 limit,
-and bit-for-bit repeatability."""
+column's ranks, ranks up to 64, many columns, ACA storage, extreme scales of Phi, wide n1 (i1
+tiles), and bit-for-bit repeatability."""
 import numpy as np
 import pytest
 
@@ -181,20 +181,14 @@ def test_mode1_n1_160_single_buffer(p):
     assert rel_cols(P, Po).max() < RTOL
 
 
-def test_mode1_wide_n1_and_limit():
-    n = (200, 5, 3)   # n1 = 200: A takes 400 TMEM columns, N blocks of 32 rows
+@pytest.mark.parametrize("n,p", [((200, 5, 3), 16), ((232, 3, 2), 16), ((330, 3, 2), 5), ((257, 4, 3), 2)])
+def test_mode1_wide_n1(n, p):
+    # n1 = 200: A takes 2 x 224 TMEM columns, N blocks of 32 rows; n1 = 232, 330, 257: i1 tiles of
+    # 160 (two or three of them, the last partly past n1), each with its own partial sums
     w = inputs.scaled_workload("precision", n, m=3)
     h, tens = _handle(w, 1e-5)
-    P, Po = _adj(h, n, tens, 16, seed=17)
+    P, Po = _adj(h, n, tens, p, seed=17)
     assert rel_cols(P, Po).max() < RTOL
-    n = (232, 3, 2)   # beyond the tensor-memory limit
-    w = inputs.scaled_workload("precision", n, m=2)
-    h, tens = _handle(w, 1e-5)
-    Psi = zbc.colmajor(len(tens), 2, torch.complex64)
-    Phi = zbc.colmajor(3 * int(np.prod(n)), 2, torch.complex64)
-    with pytest.raises(zbc.ZbcError) as e:
-        zbc.zbc_rmatvec(h, Phi, Psi, zbc.TC_MODE1)
-    assert e.value.status == zbc.ZBC_EINVAL
 
 
 def test_mode1_repeatable():
