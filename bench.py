@@ -359,7 +359,7 @@ def run_zbc(args):
     h2d = Xh.numel() * 8 + Phih.numel() * 8
     d2h = Yh.numel() * 8 + Psih.numel() * 8
 
-    # roofline of the dominant kernel (the forward product's main kernel)
+    # roofline of the dominant kernel
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -389,7 +389,8 @@ class Mlp:
 
 
 def zbc_matvec(h: Handle, X, Y, prec=FP32_SIMT, stream=None):
-    """X: (p, ldx) complex64 (column-major m x p); Y: (p, ldy) complex64."""
+    """Y = Z X.  X: (p, ldx) complex64 (column-major m x p); Y: (p, ldy) complex64.  prec:
+    FP32_SIMT, TF32X3, BF16X3, TC2, TC_MODE1 or AUTO."""
     p = X.shape[0]
     _check(lib().zbc_matvec(h.ptr, _ptr(X), _ld(X), p, _ptr(Y), _ld(Y), prec, _stream(stream)))
     return Y
@@ -425,6 +426,8 @@ def zbc_product_status(h: Handle, stream=None):
 
 
 def zbc_rmatvec(h: Handle, Phi, Psi, prec=FP32_SIMT, stream=None):
+    """Psi = Z^H Phi.  Phi: (p, ldphi) complex64 (column-major q n_v x p); Psi: (p, ldpsi)
+    complex64.  prec: FP32_SIMT, TC_MODE1 or AUTO."""
     p = Phi.shape[0]
     _check(lib().zbc_rmatvec(h.ptr, _ptr(Phi), _ld(Phi), p, _ptr(Psi), _ld(Psi), prec, _stream(stream)))
     return Psi
