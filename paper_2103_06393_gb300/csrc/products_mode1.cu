@@ -18,18 +18,20 @@
 //   B[2 (i23l P + s) + 1][2 i1 + e'] = (Im, -Re) Phi[i1, i23, s]  -> D = Im T
 // Precision: both operands are split into fp16 hi + lo (x = hi + lo to ~2^-22 relative), after
 // scaling by powers of two into fp16's normal range -- per row of A (2^(kHalfShift - uexp)) and
-// per N block of B (2^(kHalfShift - e_blk)) -- and the three products hi.hi + hi.lo + lo.hi
-// accumulate in FP32; the scales are removed exactly in the epilogue.
+// per (N block, right-hand side) of B (2^(kHalfShift - e)) -- and the three products
+// hi.hi + hi.lo + lo.hi accumulate in FP32 over K = 2 n1 (at most 2 x 224 per sum); the scales
+// are removed exactly in the epilogue.
 //
 // Kernels, per call:
 //   phi_split_kernel      Phi -> the B operand blocks (fp16 hi / lo, one contiguous run per
-//                         (component, RHS chunk, N block, K chunk)) and one exponent per N block
-//   rmatvec_mode1_kernel  persistent, one CTA per SM; items (RHS chunk, N range, group):
+//                         (component, RHS chunk, N block, K chunk)) and the exponents
+//   rmatvec_mode1_kernel  persistent, one CTA per SM; items (RHS chunk, N range, i1 tile, group):
 //                         epilogue warps (A into TMEM, T . conj(W) sums), a copy warp
 //                         (cp.async.bulk of the B blocks into a stage ring) and an MMA warp
-//                         (A from TMEM, B from shared memory, D in TMEM: N = 256 columns with
-//                         one buffer and two epilogue warpgroups, else two buffers)
-//   mode1_reduce_kernel   Psi'[j, s] = sum over N ranges, components and ranks, fixed order
+//                         (A from TMEM, B from shared memory, D in TMEM: N = 256 or 192 columns
+//                         with one buffer and two epilogue warpgroups, else two buffers)
+//   mode1_reduce_kernel   Psi'[j, s] = sum over the partial slots (N ranges, i1 tiles, epilogue
+//                         warpgroups), components and ranks, in a fixed order
 // plus, once per handle, mode1_build_kernel (the A operand and the row table).
 #include <cuda_fp16.h>
 
@@ -86,7 +88,6 @@ int build_mode1_cache(Handle& h, cudaStream_t st) {
   if (dc.mode1) return ZBC_OK;
   const int q = h.q, M = h.M;
   std::vector<int> gbase(q + 1, 0);
-  std::vector<int64_t> rstart(q, 0);
   for (int k = 0; k < q; ++k) {
     int64_t R = 0;
     for (int j = 0; j < M; ++j) R += h.desc[(size_t)j * q + k].r1;
