@@ -67,7 +67,7 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  *             beyond n1 = 224).
  *             Forward: per block of 128 (i2 i3, RHS) rows and i1 tile of at most 96,
  *             Y^k = U1 (W X) over all (column, rank) rows, W X generated on CUDA cores, the
- *             tensor-core sum folded into FP32 every 96 rows.
+ *             tensor-core sum folded into FP32 every 192 rows.
  * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
  *             right-hand-side class; before any tuning, BF16X3 for the forward product when
  *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,

@@ -1,6 +1,6 @@
 """The forward product Y = Z X in its mode-1 tensor-core form (ZBC_TC_MODE1: per block of 128
 (i23, s) rows one fp16 hi/lo tcgen05 GEMM over the (column, rank) rows, A = W X generated on the
-CUDA cores into tensor memory, B = U1, the accumulator folded into FP32 registers every 3 chunks)
+CUDA cores into tensor memory, B = U1, the accumulator folded into FP32 registers every 6 chunks)
 against the FP64 oracle on the same compressed data: 4, 8 and 16 right-hand sides per pass,
 several passes, ragged grids (n1 not a multiple of 16, i23 blocks cut by the end of n2 n3), i1
 tiles (n1 > 96), chunks that hold one column or 32, ranks up to 64, ACA storage, extreme and mixed
