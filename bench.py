@@ -401,10 +401,10 @@ def run_zbc(args):
                         ("rmatvec_simt_kernel", "adj_simt6"): 3.222e9 + 0.003e9,
                         ("matvec_tc_kernel", "fwd_tf32x3"): 2.9106e9 + 0.3299e9,
                         ("matvec_tc_kernel", "tf32x3"): 2.9106e9 + 0.3299e9,
-                        ("matvec_mode1_kernel", "fwd_mode1"): 2.9919e9 + 0.3318e9,
-                        ("matvec_mode1_kernel", "tc_mode1"): 2.9919e9 + 0.3318e9,
-                        ("rmatvec_mode1_kernel", "adj_mode1"): 3.8652e9 + 0.0402e9,
-                        ("rmatvec_mode1_kernel", "tc_mode1"): 3.8652e9 + 0.0402e9}
+                        ("matvec_mode1_kernel", "fwd_mode1"): 2.9775e9 + 0.3334e9,
+                        ("matvec_mode1_kernel", "tc_mode1"): 2.9775e9 + 0.3334e9,
+                        ("rmatvec_mode1_kernel", "adj_mode1"): 3.8657e9 + 0.0406e9,
+                        ("rmatvec_mode1_kernel", "tc_mode1"): 3.8657e9 + 0.0406e9}
     dom_variant = variant["forward"] if dom_fwd else variant["adjoint"]
     if not args.columns:
         roof["traffic"] = measured_traffic.get((kern, dom_variant))
