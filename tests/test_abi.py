@@ -42,3 +42,17 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(zbc, "_lib", None)
     with pytest.raises(ImportError):
         zbc.lib()
+
+
+def test_binding_enums_match_the_header():
+    # the Python binding's integer constants are the header's enum values (zbc_precision and the
+    # status codes), and zbc_tune's variant list has the length the header documents
+    from paper_2103_06393_gb300 import zbc
+    text = open(os.path.join(ROOT, "include", "zbc.h")).read()
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ZBC_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    for name in ("FP32_SIMT", "TF32X3", "BF16X3", "AUTO", "TC2", "TC_MODE1"):
+        assert getattr(zbc, name) == values["ZBC_" + name], name
+    for name in ("ZBC_OK", "ZBC_EINVAL"):
+        assert getattr(zbc, name) == values[name], name
+    m = re.search(r"times_ms_host : optional float\[(\d+)\]", text)
+    assert m and int(m.group(1)) == len(zbc.TUNE_VARIANTS)
