@@ -344,12 +344,25 @@ def run_zbc(args):
     Yh = torch.empty(Yd.shape, dtype=Yd.dtype).pin_memory()
     Psih = torch.empty(Psid.shape, dtype=Psid.dtype).pin_memory()
 
+    # the copies run on a second stream where the data flow allows: Phi's upload beside the
+    # forward product, Y's download beside the adjoint; the step ends when every copy has
+    copy_stream = torch.cuda.Stream()
+
     def e2e_step():
+        main = torch.cuda.current_stream()
+        copy_stream.wait_stream(main)            # the previous step is done with Phi and Y
+        with torch.cuda.stream(copy_stream):
+            Phid.copy_(Phih, non_blocking=True)
+        phi_ready = copy_stream.record_event()
         Xd.copy_(Xh, non_blocking=True)
-        Phid.copy_(Phih, non_blocking=True)
-        step()
-        Yh.copy_(Yd, non_blocking=True)
+        zbc.zbc_matvec(h, Xd, Yd, fcode)
+        copy_stream.wait_stream(main)
+        with torch.cuda.stream(copy_stream):
+            Yh.copy_(Yd, non_blocking=True)
+        main.wait_event(phi_ready)
+        zbc.zbc_rmatvec(h, Phid, Psid, acode)
         Psih.copy_(Psid, non_blocking=True)
+        main.wait_stream(copy_stream)
 
     for _ in range(2):
         e2e_step()
