@@ -1,15 +1,21 @@
-"""Coupling-matrix entries from the free-space dyadic Green's function (FP64).
+"""Coupling-matrix entries from the free-space Green's function (FP64).
 
 Paper: Eq. n6 gives the scalar Helmholtz kernel g = exp(-i k0 R) / (4 pi R); Eq. nNt
-defines the N operator built on it; Sec. III.A says each column of the coupling
-matrix is the concatenation of q per-component vectors over the voxels, reshaped
+defines the N operator built on it and Eq. nKt the K operator (curl of the single-layer
+potential) that maps coil currents to magnetic fields; Sec. III.A says each column of the
+coupling matrix is the concatenation of q per-component vectors over the voxels, reshaped
 column-major into n1 x n2 x n3 tensors (Fig. 2).
 
-Point-matched form used here (one quadrature point per voxel and per segment):
-    Z[(k, v), e] = h^3 * len_e * [ G(r_v - c_e) t_e ]_k,   G = (I + grad grad / k0^2) g
-with, for R = |r_v - c_e|, Rhat the unit vector and x = k0 R,
-    G = g * [ (1 - i/x - 1/x^2) I + (-1 + 3i/x + 3/x^2) Rhat Rhat^T ].
-The closed form follows from grad grad g = g'' Rhat Rhat + (g'/R)(I - Rhat Rhat).
+Point-matched form used here (one point per voxel; the segment either point-matched at its
+centre or integrated with an nq-point Gauss-Legendre rule along it):
+    Z[(k, v), e] = h^3 * len_e * sum_q (w_q / 2) [ Kern(r_v - p_eq) t_e ]_k,
+    p_eq = c_e + (xi_q len_e / 2) t_e,   (xi_q, w_q) the Gauss-Legendre rule on [-1, 1],
+with Kern = G = (I + grad grad / k0^2) g (the N operator) or Kern t = grad g x t (the K
+operator, curl(g t) for a constant t).  For R = |r_v - p|, Rhat the unit vector, x = k0 R:
+    G = g * [ (1 - i/x - 1/x^2) I + (-1 + 3i/x + 3/x^2) Rhat Rhat^T ],
+    grad g = g' Rhat,   g' = -g (i k0 + 1/R).
+The closed form of G follows from grad grad g = g'' Rhat Rhat + (g'/R)(I - Rhat Rhat).  One
+point (xi = 0, w = 2) is the plain point-matched form.
 Row index (k, v) -> k*n_v + v  (Algorithm 1: Y = [Y^1; ...; Y^q]).
 """
 import numpy as np
@@ -39,6 +45,37 @@ def dyadic_green(r_obs: np.ndarray, r_src: np.ndarray, k0: float) -> np.ndarray:
     return g[..., None, None] * (a[..., None, None] * eye + b[..., None, None] * Rh[..., :, None] * Rh[..., None, :])
 
 
+def curl_green(r_obs: np.ndarray, r_src: np.ndarray, t: np.ndarray, k0: float) -> np.ndarray:
+    """grad g (r_obs - r_src) x t = curl(g t) for a constant t (Eq. nKt's kernel on a segment);
+    inputs (..., 3), output (..., 3)."""
+    Rv = np.asarray(r_obs, dtype=np.float64) - np.asarray(r_src, dtype=np.float64)
+    R = np.asarray(np.sqrt((Rv * Rv).sum(axis=-1)))
+    Rh = Rv / R[..., None]
+    gp = -np.asarray(scalar_green(R, k0)) * (1j * k0 + 1.0 / R)    # g'(R)
+    return gp[..., None] * np.cross(Rh, np.broadcast_to(t, Rh.shape))
+
+
+def gauss_legendre(nq: int):
+    """Nodes and weights of the nq-point Gauss-Legendre rule on [-1, 1] (library routine)."""
+    x, w = np.polynomial.legendre.leggauss(int(nq))
+    return x, w
+
+
+def segment_field(rv: np.ndarray, centre, tangent, length, k0: float, operator: str, nq: int) -> np.ndarray:
+    """sum_q (w_q / 2) Kern(rv - p_q) t over the segment's quadrature points; rv (nv, 3) -> (nv, 3)."""
+    xs, ws = gauss_legendre(nq)
+    f = np.zeros((rv.shape[0], 3), dtype=np.complex128)
+    for xq, wq in zip(xs, ws):
+        p = np.asarray(centre, dtype=np.float64) + 0.5 * xq * length * np.asarray(tangent, dtype=np.float64)
+        if operator == "N":
+            f += 0.5 * wq * (dyadic_green(rv, p[None, :], k0) @ tangent)
+        elif operator == "K":
+            f += 0.5 * wq * curl_green(rv, p[None, :], tangent, k0)
+        else:
+            raise ValueError(operator)
+    return f
+
+
 def voxel_centres(n1: int, n2: int, n3: int, h: float) -> np.ndarray:
     """(n_v, 3) centres, v = i1 + n1*(i2 + n2*i3), centred at the origin."""
     a1 = (np.arange(n1) - (n1 - 1) / 2.0) * h
@@ -59,11 +96,12 @@ def voxel_mask(n1, n2, n3, h, mask_radius) -> np.ndarray:
 
 
 def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_radius=0.0,
-                     rows=None) -> np.ndarray:
+                     rows=None, operator="N", nq=1) -> np.ndarray:
     """Dense columns Z[:, cols] of the (q*n_v) x m coupling matrix, complex128, column-major.
 
     rows: optional subset of voxel indices v; the result then has q*len(rows) rows
-    ordered (k, row-position).
+    ordered (k, row-position).  operator: "N" (Eq. nNt, the dyadic kernel) or "K" (Eq. nKt);
+    nq: Gauss-Legendre points along each segment (1 = point-matched at the centre).
     """
     assert q == 3
     n1, n2, n3 = n
@@ -78,8 +116,10 @@ def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_rad
     cols = np.atleast_1d(np.asarray(cols))
     out = np.zeros((q * nv, cols.size), dtype=np.complex128, order="F")
     for jj, e in enumerate(cols):
-        G = dyadic_green(rv, centre[e][None, :], k0)          # (nv, 3, 3)
-        f = G @ tangent[e]                                     # (nv, 3)
+        if operator == "N" and nq == 1:
+            f = dyadic_green(rv, centre[e][None, :], k0) @ tangent[e]   # (nv, 3)
+        else:
+            f = segment_field(rv, centre[e], tangent[e], length[e], k0, operator, nq)
         f *= h ** 3 * length[e]
         f[~keep] = 0.0
         for k in range(q):

@@ -136,7 +136,7 @@ def test_tc_long_i1_many_columns(prec):
     assert rel_cols(Y, Yo).max() < RTOL
 
 
-@pytest.mark.parametrize("prec", [zbc.FP32_SIMT, zbc.TF32X3, zbc.TC2])
+@pytest.mark.parametrize("prec", [zbc.FP32_SIMT, zbc.TF32X3, zbc.TC2, zbc.TC_MODE1])
 def test_twelve_components_per_column(prec):
     # q = 12 (a piecewise-linear basis: 4 functions x 3 components per voxel): the product
     # kernels take q from the handle, four times the work of q = 3
@@ -161,7 +161,7 @@ def test_twelve_components_per_column(prec):
     zbc.zbc_matvec(h, zbc.to_colmajor(X), Y, prec)
     zbc.zbc_product_status(h)
     assert rel_cols(zbc.from_colmajor(Y), products.matvec(tens, n, X)).max() < RTOL
-    if prec == zbc.FP32_SIMT:
+    if prec in (zbc.FP32_SIMT, zbc.TC_MODE1):
         Phi = inputs.cn01((12 * grid.nv, p), seed=8).astype(np.complex64)
         Psi = zbc.colmajor(9, p, torch.complex64)
         zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)

@@ -117,3 +117,107 @@ def test_mask_zeroes_outer_voxels():
     for k in range(3):
         seg = z[k * g.nv:(k + 1) * g.nv, 0]
         assert np.all(seg[~keep] == 0) and np.all(seg[keep] != 0)
+
+
+# ------------------------------------------------------------------------------------------------
+# the K operator (Eq. nKt: curl of the single-layer potential) and the segment quadrature
+# ------------------------------------------------------------------------------------------------
+
+def _fd_grad(r, k0, step):
+    """grad g by central first differences of the scalar kernel only."""
+    def g(x):
+        return greens.scalar_green(np.linalg.norm(x), k0)
+    e = np.eye(3) * step
+    return np.array([(g(r + e[a]) - g(r - e[a])) / (2 * step) for a in range(3)])
+
+
+@pytest.mark.parametrize("r", [np.array([0.05, -0.03, 0.02]), np.array([0.2, 0.1, -0.3]), np.array([0.0, 0.0, 0.4])])
+def test_curl_green_matches_finite_differences(r):
+    t = np.array([0.3, -0.8, 0.52])
+    t /= np.linalg.norm(t)
+    K = greens.curl_green(r, np.zeros(3), t, K0)
+    Kfd = np.cross(_fd_grad(r, K0, 1e-5 * np.linalg.norm(r)), t)
+    assert np.max(np.abs(K - Kfd)) / np.max(np.abs(K)) < 1e-8
+
+
+def test_curl_green_orthogonality_and_magnitude():
+    # grad g x t is orthogonal to t and to Rhat; |grad g x t| = |g| |i k0 + 1/R| |Rhat x t|;
+    # it vanishes for t along Rhat and changes sign with the source-observer swap
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        r, c = rng.normal(size=3) * 0.2, rng.normal(size=3) * 0.05
+        t = rng.normal(size=3)
+        t /= np.linalg.norm(t)
+        K = greens.curl_green(r, c, t, K0)
+        R = r - c
+        Rn = np.linalg.norm(R)
+        assert abs(np.dot(K, t)) < 1e-13 * np.linalg.norm(K)
+        assert abs(np.dot(K, R / Rn)) < 1e-13 * np.linalg.norm(K)
+        mag = abs(greens.scalar_green(Rn, K0)) * abs(1j * K0 + 1 / Rn) * np.linalg.norm(np.cross(R / Rn, t))
+        assert np.isclose(np.linalg.norm(K), mag, rtol=1e-13)
+        assert np.allclose(greens.curl_green(c, r, t, K0), -K, rtol=1e-13, atol=0)
+        assert np.max(np.abs(greens.curl_green(r, c, R / Rn, K0))) < 1e-15 * np.max(np.abs(K)) + 1e-300
+
+
+def test_curl_of_k_field_is_k0_squared_times_n_field():
+    # curl(curl(g t)) = curl curl (g t) = k0^2 (I + grad grad / k0^2) g t away from the source:
+    # a finite-difference curl of the K kernel gives k0^2 times the N kernel (each operator is
+    # pinned independently above; this ties the two together)
+    t = np.array([0.1, 0.7, -0.2])
+    t /= np.linalg.norm(t)
+    r = np.array([0.12, -0.05, 0.2])
+    step = 1e-5
+
+    def Kf(x):
+        return greens.curl_green(x, np.zeros(3), t, K0)
+    e = np.eye(3) * step
+    J = np.array([(Kf(r + e[a]) - Kf(r - e[a])) / (2 * step) for a in range(3)])   # J[a, b] = d_a K_b
+    curl = np.array([J[1, 2] - J[2, 1], J[2, 0] - J[0, 2], J[0, 1] - J[1, 0]])
+    N = greens.dyadic_green(r, np.zeros(3), K0) @ t
+    assert np.max(np.abs(curl - K0 ** 2 * N)) / np.max(np.abs(K0 ** 2 * N)) < 1e-7
+
+
+@pytest.mark.parametrize("operator", ["N", "K"])
+def test_segment_quadrature(operator):
+    # one Gauss-Legendre point is the point-matched form; nq points agree with a fine midpoint rule
+    # along the segment (brute force), and 8 points already to 1e-12 for a voxel 20 lengths away
+    rng = np.random.default_rng(9)
+    c = np.array([0.1, 0.0, 0.02])
+    t = rng.normal(size=3)
+    t /= np.linalg.norm(t)
+    L = 0.015
+    rv = np.array([[0.4, 0.2, -0.1], [0.12, 0.01, 0.03]])
+    one = greens.segment_field(rv, c, t, L, K0, operator, 1)
+    if operator == "N":
+        point = greens.dyadic_green(rv, c[None, :], K0) @ t
+    else:
+        point = greens.curl_green(rv, c[None, :], t, K0)
+    assert np.allclose(one, point, rtol=1e-15, atol=0)
+    nmid = 4000
+    xs = (np.arange(nmid) + 0.5) / nmid * 2 - 1
+    brute = np.zeros_like(one)
+    for x in xs:
+        p = c + 0.5 * x * L * t
+        if operator == "N":
+            brute += (greens.dyadic_green(rv, p[None, :], K0) @ t) / nmid
+        else:
+            brute += greens.curl_green(rv, p[None, :], t, K0) / nmid
+    q8 = greens.segment_field(rv, c, t, L, K0, operator, 8)
+    assert np.max(np.abs(q8 - brute)) / np.max(np.abs(brute)) < 1e-6          # the midpoint rule's own error
+    q16 = greens.segment_field(rv[:1], c, t, L, K0, operator, 16)
+    assert np.max(np.abs(q8[:1] - q16)) / np.max(np.abs(q16)) < 1e-12
+
+
+def test_k_assembly_columns():
+    # the K columns: entry by the closed form, orthogonal to the segment's tangent at every voxel
+    w = inputs.scaled_workload("tiny", (6, 5, 4), m=3)
+    g, s = w.grid, w.segments
+    Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(3), operator="K")
+    nv = g.nv
+    rv = greens.voxel_centres(*g.shape, g.h)
+    for e in range(3):
+        F = np.stack([Z[k * nv:(k + 1) * nv, e] for k in range(3)], axis=1)
+        assert np.max(np.abs(F @ s.tangent[e])) < 1e-13 * np.max(np.abs(F))
+        v = 17
+        ref = g.h ** 3 * s.length[e] * greens.curl_green(rv[v], s.centre[e], s.tangent[e], greens.wavenumber(w.freq_hz))
+        assert np.allclose(F[v], ref, rtol=1e-14, atol=0)
