@@ -143,6 +143,26 @@ int vsie_assemble_columns(const zbc_grid* g, const zbc_segments* s, double freq_
                           const int32_t* cols, int ncols, int q,
                           void* out, int64_t ld, zbc_dtype dt, zbc_stream stream);
 
+/* Green's function operator of the coupling matrix: N (Eq. nNt, the dyadic kernel above, the
+ * electric-field coupling) or K (Eq. nKt, the curl of the single-layer potential, the
+ * magnetic-field coupling Z_bc of the paper's GMT application). */
+typedef enum { ZBC_OP_N = 0, ZBC_OP_K = 1 } zbc_operator;
+
+/*
+ * vsie_assemble_columns_op -- vsie_assemble_columns with a choice of operator and a
+ * Gauss-Legendre rule of nq points (1 .. 16) along each segment:
+ *   Z[(k,v), e] = h^3 len_e sum_q (w_q / 2) [ Kern(r_v - p_q) t_e ]_k,
+ *   p_q = c_e + xi_q len_e t_e / 2   ((xi_q, w_q) the rule on [-1, 1]),
+ *   N: Kern t = (I + grad grad / k0^2) g t,   K: Kern t = grad g x t = g' (Rhat x t),
+ *   g' = -g (i k0 + 1/R).
+ * nq = 1 with ZBC_OP_N is exactly vsie_assemble_columns.  Arguments, layout and errors as there;
+ * ZBC_EINVAL for an unknown operator or nq outside [1, 16].  A quadrature point closer than
+ * 1e-12 m to a voxel centre is a caller error that the kernel does not check.
+ */
+int vsie_assemble_columns_op(const zbc_grid* g, const zbc_segments* s, double freq_hz,
+                             const int32_t* cols, int ncols, int q, zbc_operator op, int nq,
+                             void* out, int64_t ld, zbc_dtype dt, zbc_stream stream);
+
 /*
  * tucker_compress -- column-wise Tucker compression (Sec. III.A, Fig. 2; truncated HOSVD of
  * Sec. II.B.1 with De Lathauwer's bound).

@@ -1,5 +1,6 @@
-// vsie_assemble_columns: columns of the coil-body coupling matrix (Sec. III.A; Eq. n6, Eq. nNt).
-// One thread per voxel, one grid row per requested column; FP64 arithmetic (green.cuh).
+// vsie_assemble_columns(_op): columns of the coil-body coupling matrix (Sec. III.A; Eq. n6,
+// Eq. nNt, Eq. nKt).  One thread per voxel, one grid row per requested column; FP64 arithmetic
+// (green.cuh).
 #include "green.cuh"
 
 namespace zbc {
@@ -12,7 +13,10 @@ __global__ void __launch_bounds__(256) assemble_kernel(GreenGeom G, const int32_
   if (v >= nv) return;
   const int jj = blockIdx.y;
   double2 z[3];
-  green_entry(G, v, cols[jj], z);
+  if (G.op == 0 && G.nq == 1)
+    green_entry(G, v, cols[jj], z);
+  else
+    segment_entry(G, v, cols[jj], z);
   OutT* o = out + ld * jj + v;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -36,6 +40,10 @@ GreenGeom make_green(const zbc_grid* g, const zbc_segments* s, double freq_hz) {
   G.tangent = s->tangent;
   G.length = s->length;
   G.m = s->m;
+  G.op = 0;
+  G.nq = 1;
+  G.qx[0] = 0.0;
+  G.qw[0] = 2.0;
   return G;
 }
 
@@ -56,8 +64,16 @@ using namespace zbc;
 extern "C" int vsie_assemble_columns(const zbc_grid* g, const zbc_segments* s, double freq_hz,
                                      const int32_t* cols, int ncols, int q, void* out, int64_t ld,
                                      zbc_dtype dt, zbc_stream stream) {
+  return vsie_assemble_columns_op(g, s, freq_hz, cols, ncols, q, ZBC_OP_N, 1, out, ld, dt, stream);
+}
+
+extern "C" int vsie_assemble_columns_op(const zbc_grid* g, const zbc_segments* s, double freq_hz,
+                                        const int32_t* cols, int ncols, int q, zbc_operator op, int nq, void* out,
+                                        int64_t ld, zbc_dtype dt, zbc_stream stream) {
   clear_error();
   ZBC_CHECK_ARG(g && s && cols && out, "vsie_assemble_columns: null argument");
+  ZBC_CHECK_ARG(op == ZBC_OP_N || op == ZBC_OP_K, "unknown operator %d", (int)op);
+  ZBC_CHECK_ARG(nq >= 1 && nq <= kMaxQuad, "nq must be in [1, %d]", kMaxQuad);
   ZBC_CHECK_ARG(q == 3, "q must be 3");
   ZBC_CHECK_ARG(g->n1 >= 1 && g->n2 >= 1 && g->n3 >= 1 && g->h > 0, "bad grid");
   ZBC_CHECK_ARG(s->m >= 1 && s->centre && s->tangent && s->length, "bad segments");
@@ -67,7 +83,10 @@ extern "C" int vsie_assemble_columns(const zbc_grid* g, const zbc_segments* s, d
   ZBC_CHECK_ARG(ld >= 3 * nv, "ld (%lld) < q*n_v (%lld)", (long long)ld, (long long)(3 * nv));
   ZBC_CHECK_ARG(dt == ZBC_C64 || dt == ZBC_C128, "bad dtype");
   if (ncols == 0) return ZBC_OK;
-  const GreenGeom G = make_green(g, s, freq_hz);
+  GreenGeom G = make_green(g, s, freq_hz);
+  G.op = op == ZBC_OP_K ? 1 : 0;
+  G.nq = nq;
+  gauss_legendre(nq, G.qx, G.qw);
   dim3 grid((unsigned)ceil_div(nv, 256), (unsigned)ncols);
   if (dt == ZBC_C128)
     assemble_kernel<double2><<<grid, 256, 0, stream>>>(G, cols, (double2*)out, ld);

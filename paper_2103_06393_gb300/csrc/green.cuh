@@ -1,8 +1,13 @@
-// Coupling-matrix entries from the dyadic Green's function (Sec. III.A; Eq. n6, Eq. nNt), FP64.
+// Coupling-matrix entries from the free-space Green's function (Sec. III.A; Eq. n6, Eq. nNt,
+// Eq. nKt), FP64.
 //
-// Z[(k,v), e] = h^3 len_e [ (I + grad grad / k0^2) g(r_v - c_e) t_e ]_k with
+// Point-matched at the segment centre (green_entry, the N operator):
+//   Z[(k,v), e] = h^3 len_e [ (I + grad grad / k0^2) g(r_v - c_e) t_e ]_k with
 // g = exp(-i k0 R)/(4 pi R) and, for x = k0 R and Rhat = (r_v - c_e)/R,
 //   (I + grad grad/k0^2) g = g [ (1 - i/x - 1/x^2) I + (-1 + 3i/x + 3/x^2) Rhat Rhat^T ].
+// With an nq-point Gauss-Legendre rule along the segment (segment_entry), the N or the K operator:
+//   Z[(k,v), e] = h^3 len_e sum_q (w_q / 2) [ Kern(r_v - p_q) t_e ]_k,  p_q = c_e + xi_q len_e t_e / 2,
+//   K: Kern t = grad g x t = g' (Rhat x t),  g' = -g (i k0 + 1/R).
 #pragma once
 
 #include <cmath>
@@ -11,6 +16,8 @@
 
 namespace zbc {
 
+constexpr int kMaxQuad = 16;  // Gauss-Legendre points per segment, at most
+
 struct GreenGeom {
   int n1, n2, n3;
   double h, mask_r, k0;
@@ -18,6 +25,10 @@ struct GreenGeom {
   const double* tangent;
   const double* length;
   int m;
+  int op;                   // 0: N operator (Eq. nNt), 1: K operator (Eq. nKt)
+  int nq;                   // quadrature points along the segment
+  double qx[kMaxQuad];      // nodes on [-1, 1]
+  double qw[kMaxQuad];      // weights (sum 2)
 };
 
 // voxel centre (same rounding as ((i - (n-1)/2) * h)) and the mask decision
@@ -61,6 +72,87 @@ __device__ __forceinline__ void green_entry(const GreenGeom& G, int64_t v, int e
   }
 }
 
+// sum over the segment's quadrature points of (w_q / 2) Kern(r_v - p_q) t_e, times h^3 len_e;
+// zero for masked voxels or e outside [0, m)
+__device__ __forceinline__ void segment_entry(const GreenGeom& G, int64_t v, int e, double2 (&out)[3]) {
+  double x, y, z;
+  const bool keep = voxel_centre(G, v, x, y, z) && e >= 0 && e < G.m;
+  double accr[3] = {0.0, 0.0, 0.0}, acci[3] = {0.0, 0.0, 0.0};
+  if (keep) {
+    const double tx = G.tangent[3 * e + 0], ty = G.tangent[3 * e + 1], tz = G.tangent[3 * e + 2];
+    const double len = G.length[e];
+    for (int iq = 0; iq < G.nq; ++iq) {
+      const double off = 0.5 * G.qx[iq] * len;
+      const double Rx = x - (G.centre[3 * e + 0] + off * tx), Ry = y - (G.centre[3 * e + 1] + off * ty),
+                   Rz = z - (G.centre[3 * e + 2] + off * tz);
+      const double R = sqrt(Rx * Rx + Ry * Ry + Rz * Rz);
+      const double iR = 1.0 / R;
+      const double hx = Rx * iR, hy = Ry * iR, hz = Rz * iR;
+      double s, c;
+      sincos(G.k0 * R, &s, &c);
+      const double wq = 0.5 * G.qw[iq] / (4.0 * M_PI * R);
+      const double gr = wq * c, gi = -wq * s;  // (w_q / 2) g
+      double ur[3], ui[3];
+      if (G.op == 0) {
+        const double kr = G.k0 * R, ikr = 1.0 / kr, ikr2 = ikr * ikr;
+        const double ar = 1.0 - ikr2, ai = -ikr, br = -1.0 + 3.0 * ikr2, bi = 3.0 * ikr;
+        const double ht = hx * tx + hy * ty + hz * tz;
+        const double tk[3] = {tx, ty, tz}, hk[3] = {hx, hy, hz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ur[k] = ar * tk[k] + br * hk[k] * ht;
+          ui[k] = ai * tk[k] + bi * hk[k] * ht;
+        }
+      } else {
+        // g' / g = -(i k0 + 1/R) = -1/R - i k0; Rhat x t
+        const double cx = hy * tz - hz * ty, cy = hz * tx - hx * tz, cz = hx * ty - hy * tx;
+        const double pr = -iR, pi = -G.k0;
+        const double ck[3] = {cx, cy, cz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ur[k] = pr * ck[k];
+          ui[k] = pi * ck[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        accr[k] += gr * ur[k] - gi * ui[k];
+        acci[k] += gr * ui[k] + gi * ur[k];
+      }
+    }
+    const double sc = G.h * G.h * G.h * len;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      accr[k] *= sc;
+      acci[k] *= sc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) out[k] = make_double2(accr[k], acci[k]);
+}
+
 inline double wavenumber(double freq_hz) { return 2.0 * M_PI * freq_hz / 299792458.0; }
+
+// nq-point Gauss-Legendre rule on [-1, 1]: the roots of P_nq by Newton's method from the
+// Chebyshev-like first guesses cos(pi (i - 1/4) / (nq + 1/2)), weights 2 / ((1 - x^2) P'_nq(x)^2)
+inline void gauss_legendre(int nq, double* x, double* w) {
+  for (int i = 0; i < nq; ++i) {
+    double xi = std::cos(M_PI * (i + 0.75) / (nq + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = xi;  // P_0, P_1
+      for (int k = 2; k <= nq; ++k) {
+        const double pk = ((2.0 * k - 1.0) * xi * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = nq * (xi * p1 - p0) / (xi * xi - 1.0);  // P'_nq from P_nq and P_nq-1
+      const double dx = p1 / dp;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    x[i] = xi;
+    w[i] = 2.0 / ((1.0 - xi * xi) * dp * dp);
+  }
+}
 
 }  // namespace zbc

@@ -71,6 +71,8 @@ def lib():
             "zbc_version": ([], C.c_char_p),
             "zbc_kernel_launches": ([], C.c_int64),
             "vsie_assemble_columns": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, vp, i64, i32, vp], i32),
+            "vsie_assemble_columns_op": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, i32, i32, vp, i64,
+                                          i32, vp], i32),
             "tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, i32, C.POINTER(vp),
                                  C.POINTER(zbc_compress_stats), vp], i32),
             "zbc_matvec": ([vp, vp, i64, i32, vp, i64, i32, vp], i32),
@@ -279,6 +281,9 @@ class DeviceSegments:
         return zbc_segments(self.m, self.centre.data_ptr(), self.tangent.data_ptr(), self.length.data_ptr())
 
 
+OP_N, OP_K = 0, 1
+
+
 def vsie_assemble_columns(grid, dsegs: DeviceSegments, freq_hz: float, cols, out, q=3, stream=None):
     """cols: int32 CUDA tensor; out: column-major buffer (ncols, ld) complex64/complex128."""
     import torch
@@ -287,6 +292,19 @@ def vsie_assemble_columns(grid, dsegs: DeviceSegments, freq_hz: float, cols, out
     dt = C128 if out.dtype == torch.complex128 else C64
     _check(lib().vsie_assemble_columns(C.byref(g), C.byref(s), freq_hz, _ptr(cols), int(cols.numel()), q, _ptr(out),
                                        _ld(out), dt, _stream(stream)))
+    return out
+
+
+def vsie_assemble_columns_op(grid, dsegs: DeviceSegments, freq_hz: float, cols, out, op=OP_N, nq=1, q=3,
+                             stream=None):
+    """vsie_assemble_columns with the operator (OP_N: Eq. nNt, OP_K: Eq. nKt) and nq Gauss-Legendre
+    points along each segment."""
+    import torch
+    g = grid_struct(grid)
+    s = dsegs.struct()
+    dt = C128 if out.dtype == torch.complex128 else C64
+    _check(lib().vsie_assemble_columns_op(C.byref(g), C.byref(s), freq_hz, _ptr(cols), int(cols.numel()), q, int(op),
+                                          int(nq), _ptr(out), _ld(out), dt, _stream(stream)))
     return out
 
 
