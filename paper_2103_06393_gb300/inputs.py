@@ -77,6 +77,33 @@ def circle_coil(radius: float, m: int) -> Segments:
     return Segments(c, t, ln)
 
 
+def loop_coil_y(radius: float, d: float, m: int) -> Segments:
+    """m straight segments on the loop of the given radius in the plane y = d, centred at
+    (0, d, 0): phi_e = 2*pi*(e + 1/2)/m, centre (r cos phi, d, r sin phi), tangent
+    (-sin phi, 0, cos phi), length 2*pi*r/m (the loop-and-cube geometry of the rank studies)."""
+    phi = 2.0 * np.pi * (np.arange(m) + 0.5) / m
+    c = np.stack([radius * np.cos(phi), np.full(m, d), radius * np.sin(phi)], axis=1)
+    t = np.stack([-np.sin(phi), np.zeros(m), np.cos(phi)], axis=1)
+    return Segments(c, t, np.full(m, 2.0 * np.pi * radius / m))
+
+
+def triangle_coil_y(circumradius: float, d: float, n_per_side: int) -> Segments:
+    """The sides of an equilateral triangle in the plane y = d with centroid (0, d, 0) and one
+    vertex at (0, d, circumradius), each side cut into n_per_side equal straight segments."""
+    ang = np.pi / 2 + 2.0 * np.pi * np.arange(3) / 3
+    verts = np.stack([circumradius * np.cos(ang), np.full(3, d), circumradius * np.sin(ang)], axis=1)
+    cs, ts, ls = [], [], []
+    for a in range(3):
+        p0, p1 = verts[a], verts[(a + 1) % 3]
+        side = p1 - p0
+        L = float(np.linalg.norm(side))
+        for i in range(n_per_side):
+            cs.append(p0 + side * (i + 0.5) / n_per_side)
+            ts.append(side / L)
+            ls.append(L / n_per_side)
+    return Segments(np.array(cs), np.array(ts), np.array(ls))
+
+
 def _largest_remainder(total: int, weights) -> list:
     w = np.asarray(weights, dtype=np.float64)
     raw = total * w / w.sum()

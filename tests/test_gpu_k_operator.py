@@ -95,3 +95,16 @@ def test_k_columns_compress_and_multiply(prec):
     zbc.zbc_product_status(h)
     assert rel_cols(zbc.from_colmajor(Y), products.matvec(tens, g.shape, X.astype(np.complex128))).max() < 1e-5
     assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, g.shape, Phi.astype(np.complex128))).max() < 1e-5
+
+
+@pytest.mark.parametrize("d,oracle_rank", [(0.55, 16), (1.0, 11)])
+def test_gpu_compressor_reproduces_the_distance_study(d, oracle_rank):
+    # the rank-vs-distance study (tests/test_oracle_rank_trends.py) through the GPU path: K columns
+    # with 4-point quadrature assembled and HOSVD-compressed on the GPU give the oracle's max rank
+    g = inputs.Grid(16, 16, 16, 1.0 / 16)
+    s = inputs.loop_coil_y(0.5, d, 24)
+    w = inputs.Workload("rank-distance", g, s, 298.06e6, 1e-8, 1)
+    Zd = zbc.to_colmajor(_assemble(w, "K", 4))
+    h, st = zbc.tucker_compress(Zd, g, 1e-8)
+    assert abs(st.max_rank - oracle_rank) <= 1
+    assert st.max_rel_err <= 1e-8 * (1 + 1e-9)
