@@ -16,7 +16,10 @@ operator, curl(g t) for a constant t).  For R = |r_v - p|, Rhat the unit vector,
     grad g = g' Rhat,   g' = -g (i k0 + 1/R).
 The closed form of G follows from grad grad g = g'' Rhat Rhat + (g'/R)(I - Rhat Rhat).  One
 point (xi = 0, w = 2) is the plain point-matched form.
-Row index (k, v) -> k*n_v + v  (Algorithm 1: Y = [Y^1; ...; Y^q]).
+Row index (k, v) -> k*n_v + v  (Algorithm 1: Y = [Y^1; ...; Y^q]).  For the piecewise-linear
+basis (q = 12, Sec. II.A) each voxel carries phi_0 = 1 and the three linear functions
+(x - x_c)/h, (y - y_c)/h, (z - z_c)/h per field component, integrated over the voxel with a
+2 x 2 x 2 Gauss-Legendre rule; row block b = 3 l + k.
 """
 import numpy as np
 
@@ -76,6 +79,25 @@ def segment_field(rv: np.ndarray, centre, tangent, length, k0: float, operator: 
     return f
 
 
+def pwl_field(rv: np.ndarray, h: float, centre, tangent, length, k0: float, operator: str, nq: int,
+              nvq: int = 2) -> np.ndarray:
+    """Piecewise-linear voxel basis (q = 12): for each voxel centre rv (nv, 3), the four basis
+    functions phi_0 = 1, phi_1 = (x - x_c)/h, phi_2 = (y - y_c)/h, phi_3 = (z - z_c)/h integrated
+    against the segment's field with an nvq^3 Gauss-Legendre rule over the voxel (mean over the
+    voxel, i.e. divided by h^3).  Returns (nv, 4, 3): [basis l][component k]."""
+    xs, ws = gauss_legendre(nvq)
+    out = np.zeros((rv.shape[0], 4, 3), dtype=np.complex128)
+    for ix, wx in zip(xs, ws):
+        for iy, wy in zip(xs, ws):
+            for iz, wz in zip(xs, ws):
+                d = 0.5 * np.array([ix, iy, iz])            # offset / h, in [-1/2, 1/2]^3
+                f = segment_field(rv + h * d[None, :], centre, tangent, length, k0, operator, nq)
+                wgt = wx * wy * wz / 8.0                    # the rule's weights sum to 1
+                for l, phi in enumerate((1.0, d[0], d[1], d[2])):
+                    out[:, l, :] += wgt * phi * f
+    return out
+
+
 def voxel_centres(n1: int, n2: int, n3: int, h: float) -> np.ndarray:
     """(n_v, 3) centres, v = i1 + n1*(i2 + n2*i3), centred at the origin."""
     a1 = (np.arange(n1) - (n1 - 1) / 2.0) * h
@@ -102,8 +124,11 @@ def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_rad
     rows: optional subset of voxel indices v; the result then has q*len(rows) rows
     ordered (k, row-position).  operator: "N" (Eq. nNt, the dyadic kernel) or "K" (Eq. nKt);
     nq: Gauss-Legendre points along each segment (1 = point-matched at the centre).
+    q = 3: piecewise-constant basis, point-matched at the voxel centre.  q = 12: piecewise-linear
+    basis (pwl_field, 2 x 2 x 2 Gauss points per voxel), row block b = 3 l + k for basis l and
+    component k.
     """
-    assert q == 3
+    assert q in (3, 12)
     n1, n2, n3 = n
     k0 = wavenumber(freq_hz)
     rv = voxel_centres(n1, n2, n3, h)
@@ -116,7 +141,9 @@ def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_rad
     cols = np.atleast_1d(np.asarray(cols))
     out = np.zeros((q * nv, cols.size), dtype=np.complex128, order="F")
     for jj, e in enumerate(cols):
-        if operator == "N" and nq == 1:
+        if q == 12:
+            f = pwl_field(rv, h, centre[e], tangent[e], length[e], k0, operator, nq).reshape(nv, 12)
+        elif operator == "N" and nq == 1:
             f = dyadic_green(rv, centre[e][None, :], k0) @ tangent[e]   # (nv, 3)
         else:
             f = segment_field(rv, centre[e], tangent[e], length[e], k0, operator, nq)

@@ -221,3 +221,54 @@ def test_k_assembly_columns():
         v = 17
         ref = g.h ** 3 * s.length[e] * greens.curl_green(rv[v], s.centre[e], s.tangent[e], greens.wavenumber(w.freq_hz))
         assert np.allclose(F[v], ref, rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------------------------------------------------
+# piecewise-linear voxel basis (q = 12)
+# ------------------------------------------------------------------------------------------------
+
+_C, _T, _L = np.array([0.15, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]), 0.015
+_RV = np.array([[0.0, 0.01, 0.0], [0.1, 0.02, -0.01], [0.05, -0.05, 0.03]])
+_H = 0.005
+
+
+@pytest.mark.parametrize("op", ["N", "K"])
+def test_pwl_rule_against_a_high_order_rule(op):
+    # the 2 x 2 x 2 Gauss rule against an 8 x 8 x 8 one (library nodes): the constant rows to the
+    # rule's accuracy, the linear rows to its (lower) accuracy for the linear-times-field integrand
+    a = greens.pwl_field(_RV, _H, _C, _T, _L, K0, op, 2, nvq=2)
+    b = greens.pwl_field(_RV, _H, _C, _T, _L, K0, op, 2, nvq=8)
+    assert np.max(np.abs(a[:, 0] - b[:, 0])) / np.max(np.abs(b[:, 0])) < 1e-4
+    for l in range(1, 4):
+        assert np.max(np.abs(a[:, l] - b[:, l])) / np.max(np.abs(b[:, l])) < 5e-3
+
+
+@pytest.mark.parametrize("op", ["N", "K"])
+def test_pwl_moments(op):
+    # mean of f over the voxel = f(r_c) (1 - k0^2 h^2 / 24) + O(h^4) (the Laplacian of a Helmholtz
+    # field is -k0^2 f); the linear rows are the first moments (h / 12) d_x f, (h / 12) d_y f,
+    # (h / 12) d_z f + O(h^3), checked by central differences of the point-matched field
+    a = greens.pwl_field(_RV, _H, _C, _T, _L, K0, op, 2)
+    f0 = greens.segment_field(_RV, _C, _T, _L, K0, op, 2)
+    assert np.max(np.abs(a[:, 0] - f0 * (1 - K0 ** 2 * _H ** 2 / 24))) / np.max(np.abs(f0)) < 1e-4
+    e = 1e-6
+    for ax in range(3):
+        d = np.zeros(3)
+        d[ax] = e
+        df = (greens.segment_field(_RV + d, _C, _T, _L, K0, op, 2) - greens.segment_field(_RV - d, _C, _T, _L, K0, op, 2)) / (2 * e)
+        assert np.max(np.abs(a[:, ax + 1] - _H / 12 * df)) / np.max(np.abs(_H / 12 * df)) < 1e-2
+
+
+def test_pwl_assembly_layout():
+    # q = 12 columns: row block b = 3 l + k holds basis l, component k of pwl_field, times h^3 len
+    w = inputs.scaled_workload("tiny", (5, 4, 3), m=2)
+    g, s = w.grid, w.segments
+    Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(2), q=12,
+                                operator="K", nq=2)
+    assert Z.shape == (12 * g.nv, 2)
+    rv = greens.voxel_centres(*g.shape, g.h)
+    F = greens.pwl_field(rv, g.h, s.centre[1], s.tangent[1], s.length[1], greens.wavenumber(w.freq_hz), "K", 2)
+    for l in range(4):
+        for k in range(3):
+            b = 3 * l + k
+            assert np.allclose(Z[b * g.nv:(b + 1) * g.nv, 1], g.h ** 3 * s.length[1] * F[:, l, k], rtol=1e-14, atol=0)
