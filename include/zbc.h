@@ -155,9 +155,14 @@ typedef enum { ZBC_OP_N = 0, ZBC_OP_K = 1 } zbc_operator;
  *   p_q = c_e + xi_q len_e t_e / 2   ((xi_q, w_q) the rule on [-1, 1]),
  *   N: Kern t = (I + grad grad / k0^2) g t,   K: Kern t = grad g x t = g' (Rhat x t),
  *   g' = -g (i k0 + 1/R).
- * nq = 1 with ZBC_OP_N is exactly vsie_assemble_columns.  Arguments, layout and errors as there;
- * ZBC_EINVAL for an unknown operator or nq outside [1, 16].  A quadrature point closer than
- * 1e-12 m to a voxel centre is a caller error that the kernel does not check.
+ * q = 3: piecewise-constant basis (one point per voxel).  q = 12: piecewise-linear basis (Sec.
+ * II.A): per voxel phi_0 = 1, phi_1..3 = (x - x_c)/h, (y - y_c)/h, (z - z_c)/h for each field
+ * component, integrated over the voxel with the 2 x 2 x 2 Gauss-Legendre rule (the result is
+ * h^3 x the rule's mean); row block b = 3 l + k (basis l, component k), row b n_v + v; ld >= 12 n_v.
+ * nq = 1, q = 3 with ZBC_OP_N is exactly vsie_assemble_columns.  Arguments, layout and errors as
+ * there; ZBC_EINVAL for an unknown operator, nq outside [1, 16] or q not 3 or 12.  A quadrature
+ * point closer than 1e-12 m to a voxel's quadrature point is a caller error the kernel does not
+ * check.
  */
 int vsie_assemble_columns_op(const zbc_grid* g, const zbc_segments* s, double freq_hz,
                              const int32_t* cols, int ncols, int q, zbc_operator op, int nq,

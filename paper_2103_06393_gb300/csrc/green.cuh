@@ -72,63 +72,96 @@ __device__ __forceinline__ void green_entry(const GreenGeom& G, int64_t v, int e
   }
 }
 
-// sum over the segment's quadrature points of (w_q / 2) Kern(r_v - p_q) t_e, times h^3 len_e;
-// zero for masked voxels or e outside [0, m)
+// sum over the segment's quadrature points of (w_q / 2) Kern(r - p_q) t_e at the point r
+// (without the h^3 len_e factor): accr, acci hold the three components
+__device__ __forceinline__ void field_at(const GreenGeom& G, double x, double y, double z, int e, double (&accr)[3],
+                                         double (&acci)[3]) {
+  const double tx = G.tangent[3 * e + 0], ty = G.tangent[3 * e + 1], tz = G.tangent[3 * e + 2];
+  const double len = G.length[e];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) accr[k] = acci[k] = 0.0;
+  for (int iq = 0; iq < G.nq; ++iq) {
+    const double off = 0.5 * G.qx[iq] * len;
+    const double Rx = x - (G.centre[3 * e + 0] + off * tx), Ry = y - (G.centre[3 * e + 1] + off * ty),
+                 Rz = z - (G.centre[3 * e + 2] + off * tz);
+    const double R = sqrt(Rx * Rx + Ry * Ry + Rz * Rz);
+    const double iR = 1.0 / R;
+    const double hx = Rx * iR, hy = Ry * iR, hz = Rz * iR;
+    double s, c;
+    sincos(G.k0 * R, &s, &c);
+    const double wq = 0.5 * G.qw[iq] / (4.0 * M_PI * R);
+    const double gr = wq * c, gi = -wq * s;  // (w_q / 2) g
+    double ur[3], ui[3];
+    if (G.op == 0) {
+      const double kr = G.k0 * R, ikr = 1.0 / kr, ikr2 = ikr * ikr;
+      const double ar = 1.0 - ikr2, ai = -ikr, br = -1.0 + 3.0 * ikr2, bi = 3.0 * ikr;
+      const double ht = hx * tx + hy * ty + hz * tz;
+      const double tk[3] = {tx, ty, tz}, hk[3] = {hx, hy, hz};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ur[k] = ar * tk[k] + br * hk[k] * ht;
+        ui[k] = ai * tk[k] + bi * hk[k] * ht;
+      }
+    } else {
+      // g' / g = -(i k0 + 1/R) = -1/R - i k0; Rhat x t
+      const double cx = hy * tz - hz * ty, cy = hz * tx - hx * tz, cz = hx * ty - hy * tx;
+      const double pr = -iR, pi = -G.k0;
+      const double ck[3] = {cx, cy, cz};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ur[k] = pr * ck[k];
+        ui[k] = pi * ck[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      accr[k] += gr * ur[k] - gi * ui[k];
+      acci[k] += gr * ui[k] + gi * ur[k];
+    }
+  }
+}
+
+// the three components at the voxel centre, times h^3 len_e; zero for masked voxels or e
+// outside [0, m)
 __device__ __forceinline__ void segment_entry(const GreenGeom& G, int64_t v, int e, double2 (&out)[3]) {
   double x, y, z;
   const bool keep = voxel_centre(G, v, x, y, z) && e >= 0 && e < G.m;
-  double accr[3] = {0.0, 0.0, 0.0}, acci[3] = {0.0, 0.0, 0.0};
-  if (keep) {
-    const double tx = G.tangent[3 * e + 0], ty = G.tangent[3 * e + 1], tz = G.tangent[3 * e + 2];
-    const double len = G.length[e];
-    for (int iq = 0; iq < G.nq; ++iq) {
-      const double off = 0.5 * G.qx[iq] * len;
-      const double Rx = x - (G.centre[3 * e + 0] + off * tx), Ry = y - (G.centre[3 * e + 1] + off * ty),
-                   Rz = z - (G.centre[3 * e + 2] + off * tz);
-      const double R = sqrt(Rx * Rx + Ry * Ry + Rz * Rz);
-      const double iR = 1.0 / R;
-      const double hx = Rx * iR, hy = Ry * iR, hz = Rz * iR;
-      double s, c;
-      sincos(G.k0 * R, &s, &c);
-      const double wq = 0.5 * G.qw[iq] / (4.0 * M_PI * R);
-      const double gr = wq * c, gi = -wq * s;  // (w_q / 2) g
-      double ur[3], ui[3];
-      if (G.op == 0) {
-        const double kr = G.k0 * R, ikr = 1.0 / kr, ikr2 = ikr * ikr;
-        const double ar = 1.0 - ikr2, ai = -ikr, br = -1.0 + 3.0 * ikr2, bi = 3.0 * ikr;
-        const double ht = hx * tx + hy * ty + hz * tz;
-        const double tk[3] = {tx, ty, tz}, hk[3] = {hx, hy, hz};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          ur[k] = ar * tk[k] + br * hk[k] * ht;
-          ui[k] = ai * tk[k] + bi * hk[k] * ht;
-        }
-      } else {
-        // g' / g = -(i k0 + 1/R) = -1/R - i k0; Rhat x t
-        const double cx = hy * tz - hz * ty, cy = hz * tx - hx * tz, cz = hx * ty - hy * tx;
-        const double pr = -iR, pi = -G.k0;
-        const double ck[3] = {cx, cy, cz};
+  for (int k = 0; k < 3; ++k) out[k] = make_double2(0.0, 0.0);
+  if (!keep) return;
+  double fr[3], fi[3];
+  field_at(G, x, y, z, e, fr, fi);
+  const double sc = G.h * G.h * G.h * G.length[e];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          ur[k] = pr * ck[k];
-          ui[k] = pi * ck[k];
-        }
-      }
+  for (int k = 0; k < 3; ++k) out[k] = make_double2(sc * fr[k], sc * fi[k]);
+}
+
+// piecewise-linear basis (q = 12): phi_0 = 1, phi_1..3 = (x - x_c)/h, (y - y_c)/h, (z - z_c)/h,
+// integrated over the voxel with the 2 x 2 x 2 Gauss-Legendre rule (points at offsets
+// +-h / (2 sqrt 3) per axis, weights 1/8), times h^3 len_e; out[3 l + k] for basis l, component k
+__device__ __forceinline__ void pwl_entry(const GreenGeom& G, int64_t v, int e, double2 (&out)[12]) {
+  double x, y, z;
+  const bool keep = voxel_centre(G, v, x, y, z) && e >= 0 && e < G.m;
+#pragma unroll
+  for (int b = 0; b < 12; ++b) out[b] = make_double2(0.0, 0.0);
+  if (!keep) return;
+  const double a = 0.5 / sqrt(3.0);  // offset / h of the 2-point rule on [-1/2, 1/2]
+  for (int pt = 0; pt < 8; ++pt) {
+    const double dx = (pt & 1) ? a : -a, dy = (pt & 2) ? a : -a, dz = (pt & 4) ? a : -a;
+    double fr[3], fi[3];
+    field_at(G, x + G.h * dx, y + G.h * dy, z + G.h * dz, e, fr, fi);
+    const double phi[4] = {1.0, dx, dy, dz};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        accr[k] += gr * ur[k] - gi * ui[k];
-        acci[k] += gr * ui[k] + gi * ur[k];
+        out[3 * l + k].x += 0.125 * phi[l] * fr[k];
+        out[3 * l + k].y += 0.125 * phi[l] * fi[k];
       }
-    }
-    const double sc = G.h * G.h * G.h * len;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      accr[k] *= sc;
-      acci[k] *= sc;
-    }
   }
+  const double sc = G.h * G.h * G.h * G.length[e];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) out[k] = make_double2(accr[k], acci[k]);
+  for (int b = 0; b < 12; ++b) out[b] = make_double2(sc * out[b].x, sc * out[b].y);
 }
 
 inline double wavenumber(double freq_hz) { return 2.0 * M_PI * freq_hz / 299792458.0; }

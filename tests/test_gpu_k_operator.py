@@ -108,3 +108,49 @@ def test_gpu_compressor_reproduces_the_distance_study(d, oracle_rank):
     h, st = zbc.tucker_compress(Zd, g, 1e-8)
     assert abs(st.max_rank - oracle_rank) <= 1
     assert st.max_rel_err <= 1e-8 * (1 + 1e-9)
+
+
+def _assemble_q(w, op, nq, q, dtype=torch.complex128):
+    g, s = w.grid, w.segments
+    cd = torch.arange(s.m, dtype=torch.int32, device="cuda")
+    Z = zbc.colmajor(q * g.nv, s.m, dtype)
+    zbc.vsie_assemble_columns_op(g, zbc.DeviceSegments(s), w.freq_hz, cd, Z, op=OPS[op], nq=nq, q=q)
+    torch.cuda.synchronize()
+    return zbc.from_colmajor(Z)
+
+
+@pytest.mark.parametrize("op,nq", [("K", 2), ("N", 1), ("N", 3)])
+def test_pwl_assembly_matches_oracle(op, nq):
+    # the piecewise-linear basis (q = 12): 2 x 2 x 2 Gauss points per voxel, row block 3 l + k
+    w = inputs.scaled_workload("tiny", (14, 12, 10), m=6)
+    g, s = w.grid, w.segments
+    Zg = _assemble_q(w, op, nq, 12)
+    Zo = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m), q=12,
+                                 mask_radius=g.mask_radius, operator=op, nq=nq)
+    assert Zg.shape == Zo.shape == (12 * g.nv, s.m)
+    for b in range(12):   # each block against its own scale (the linear blocks are ~100x smaller;
+        blk = slice(b * g.nv, (b + 1) * g.nv)   # some columns of a block are exactly zero)
+        assert np.linalg.norm(Zg[blk] - Zo[blk]) <= 1e-12 * np.linalg.norm(Zo[blk]), b
+    Z32 = _assemble_q(w, op, nq, 12, torch.complex64)
+    assert rel_cols(Z32, Zo).max() < 1e-7
+
+
+@pytest.mark.parametrize("prec", [zbc.FP32_SIMT, zbc.TC_MODE1])
+def test_pwl_k_columns_compress_and_multiply(prec):
+    # q = 12 magnetic coupling columns through the GPU HOSVD and both products
+    w = inputs.scaled_workload("precision", (20, 16, 12), m=6)
+    g = w.grid
+    Zd = zbc.to_colmajor(_assemble_q(w, "K", 2, 12))
+    h, st = zbc.tucker_compress(Zd, g, 1e-6, q=12)
+    assert h.info().q == 12
+    tens, _ = h.tensors()
+    p = 6
+    X = inputs.cn01((w.segments.m, p), seed=41).astype(np.complex64)
+    Phi = inputs.cn01((12 * g.nv, p), seed=42).astype(np.complex64)
+    Y = zbc.colmajor(12 * g.nv, p, torch.complex64)
+    Psi = zbc.colmajor(w.segments.m, p, torch.complex64)
+    zbc.zbc_matvec(h, zbc.to_colmajor(X), Y, prec)
+    zbc.zbc_rmatvec(h, zbc.to_colmajor(Phi), Psi, prec)
+    zbc.zbc_product_status(h)
+    assert rel_cols(zbc.from_colmajor(Y), products.matvec(tens, g.shape, X.astype(np.complex128))).max() < 1e-5
+    assert rel_cols(zbc.from_colmajor(Psi), products.rmatvec(tens, g.shape, Phi.astype(np.complex128))).max() < 1e-5
