@@ -203,7 +203,11 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   for (void* ptr : {(void*)d_row0, (void*)d_nr, (void*)d_ck, (void*)d_gbase, (void*)d_nrows})
     if (ptr) cudaFree(ptr);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess) {  // leave the cache as it was, so that a later call can build it again
+    for (void** ptr : {(void**)&mc.Bf, (void**)&mc.Wc, (void**)&mc.ew, (void**)&mc.chunkinfo, (void**)&mc.jtab}) {
+      if (*ptr) cudaFree(*ptr);
+      *ptr = nullptr;
+    }
     set_error("mode-1 forward operand build failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
   }
