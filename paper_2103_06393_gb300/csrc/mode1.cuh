@@ -38,6 +38,7 @@ struct Mode1Cache {
   bool fwd = false;
   int n23p = 0;               // n2 n3 rounded up to 16
   std::vector<int> chbase;    // host: first chunk of each component (q + 1 entries)
+  int* d_chbase = nullptr;    // the same on the device
   uint32_t* Bf = nullptr;     // [chunk][2 terms][2 n1p rows][32 words]: U1, 128-byte swizzled
   float2* Wc = nullptr;       // [chunk][n23p][32]: W scaled per (i23, row)
   int* ew = nullptr;          // [q][n23p]: exponents of the W scaling

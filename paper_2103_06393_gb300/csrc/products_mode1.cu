@@ -44,7 +44,7 @@ namespace zbc {
 void mode1_release(Mode1Cache* c) {
   if (!c) return;
   for (void* ptr : {(void*)c->A, (void*)c->rows, (void*)c->kg_k, (void*)c->colrows, (void*)c->rowsrc, (void*)c->Bf,
-                    (void*)c->Wc, (void*)c->ew, (void*)c->chunkinfo, (void*)c->jtab})
+                    (void*)c->Wc, (void*)c->ew, (void*)c->chunkinfo, (void*)c->jtab, (void*)c->d_chbase})
     if (ptr) cudaFree(ptr);
   delete c;
 }

@@ -175,6 +175,7 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&mc.ew, sizeof(int) * (size_t)q * n23p);
   if (e == cudaSuccess) e = cudaMalloc(&mc.chunkinfo, sizeof(int2) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&mc.jtab, (size_t)NC * kFwdChunk);
+  if (e == cudaSuccess) e = cudaMalloc(&mc.d_chbase, sizeof(int) * (q + 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_row0, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_nr, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_ck, sizeof(int) * NC);
@@ -185,6 +186,7 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   };
   up(mc.chunkinfo, info.data(), sizeof(int2) * NC);
   up(mc.jtab, jtab.data(), jtab.size());
+  up(mc.d_chbase, chbase.data(), sizeof(int) * (q + 1));
   up(d_row0, row0.data(), sizeof(int) * NC);
   up(d_nr, nr.data(), sizeof(int) * NC);
   up(d_ck, ck.data(), sizeof(int) * NC);
@@ -204,7 +206,8 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   for (void* ptr : {(void*)d_row0, (void*)d_nr, (void*)d_ck, (void*)d_gbase, (void*)d_nrows})
     if (ptr) cudaFree(ptr);
   if (e != cudaSuccess) {  // leave the cache as it was, so that a later call can build it again
-    for (void** ptr : {(void**)&mc.Bf, (void**)&mc.Wc, (void**)&mc.ew, (void**)&mc.chunkinfo, (void**)&mc.jtab}) {
+    for (void** ptr : {(void**)&mc.Bf, (void**)&mc.Wc, (void**)&mc.ew, (void**)&mc.chunkinfo, (void**)&mc.jtab,
+                       (void**)&mc.d_chbase}) {
       if (*ptr) cudaFree(*ptr);
       *ptr = nullptr;
     }
@@ -540,15 +543,14 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
     return ZBC_EINVAL;
   }
   const size_t smem = 1024 + (size_t)prm.S * prm.stage_bytes;
-  // scaled X^T per pass, its expansion per chunk row, the exponents; the chunk table on the device
+  // scaled X^T per pass, its expansion per chunk row, the exponents (no host copies: a call can
+  // be captured in a CUDA graph)
   prm.NC = mc.chbase[h.q];
   const size_t xt_elems = (size_t)prm.nsc * h.M * P, xe_elems = (size_t)prm.nsc * prm.NC * kFwdChunk * P;
-  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (xt_elems + xe_elems) + sizeof(int) * ((size_t)prm.nsc * P + h.q + 1)));
+  ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (xt_elems + xe_elems) + sizeof(int) * (size_t)prm.nsc * P));
   float2* XT = (float2*)h.work_xt.ptr;
   float2* XE = XT + xt_elems;
   int* ex = (int*)(XE + xe_elems);
-  int* chb = ex + prm.nsc * P;
-  ZBC_TRY_CUDA(cudaMemcpyAsync(chb, mc.chbase.data(), sizeof(int) * (h.q + 1), cudaMemcpyHostToDevice, st));
   m1f_x_kernel<<<prm.nsc * P, 256, 0, st>>>(X, ldx, h.M, p, P, XT, ex);
   m1f_xe_kernel<<<ceil_div((int64_t)xe_elems, 256), 256, 0, st>>>(XT, mc.chunkinfo, mc.jtab, h.M, prm.NC, P, prm.nsc,
                                                                    XE);
@@ -559,7 +561,7 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   prm.ew = mc.ew;
   prm.XE = XE;
   prm.ex = ex;
-  prm.chbase = chb;
+  prm.chbase = mc.d_chbase;
   prm.Y = Y;
   prm.err = (int*)h.work_err.ptr;
   ZBC_TRY((set_smem_limit<matvec_mode1_kernel<P>>((int)budget)));
