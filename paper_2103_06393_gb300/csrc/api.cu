@@ -40,13 +40,10 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-void tc_release(TcPack* p);  // products_tc.cu
-
 Handle::~Handle() {
   if (d_pool) cudaFree(d_pool);
   if (d_desc) cudaFree(d_desc);
   if (d_v) cudaFree(d_v);
-  if (tc) tc_release(tc);
   if (cache) cache_release(cache);
 }
 
@@ -127,10 +124,6 @@ int handle_append(Handle* h, const std::vector<int32_t>& ranks, const float2* d_
   if (h->pool_elems != old + new_elems) {
     set_error("internal: pool size mismatch");
     return ZBC_EINVAL;
-  }
-  if (h->tc) {
-    tc_release(h->tc);
-    h->tc = nullptr;
   }
   if (h->cache) {
     cache_release(h->cache);

@@ -40,11 +40,6 @@ constexpr int kFlush = 4;       // chunks accumulated in D before it is folded i
 constexpr int kTcMaxTasks = 6;  // tasks per tile, at most (two producer warps each)
 constexpr int kTcThreads = 32 * (2 * kTcMaxTasks + 3);  // + a copy warp per half and the MMA issuer
 
-struct TcPack {
-  int dummy;
-};
-void tc_release(TcPack* p) { delete p; }
-
 template <int FMT>
 struct Fmt;
 template <>

@@ -68,7 +68,6 @@ struct TensorDesc {
   float scale_log2;   // floor(log2 ||G||_F), used for the per-column scaling of the fp16 path
 };
 
-struct TcPack;       // tensor-core operand staging, built lazily (products_tc.cu)
 struct DecompCache;  // W = G x2 U2 x3 U3 and tile-blocked U1 per tensor, built lazily (decomp_cache.cu)
 void cache_release(DecompCache* c);
 
@@ -91,7 +90,6 @@ struct Handle {
   DevBuf work_xt;        // X^T of the forward products (s-chunk padded rows)
   DevBuf work_err;       // int: set by a product kernel whose bounded wait gave up
   DevBuf work_phi;       // mode-1 adjoint: fp16 operand blocks of Phi and their exponents
-  TcPack* tc = nullptr;
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
   // autotuned choices per right-hand-side class (zbc_tune; -1 / 0 = untuned)
