@@ -240,6 +240,69 @@ int tucker_compress_randomized(const void* cols, int64_t ld, int ncols, const zb
                                zbc_stream stream);
 
 /*
+ * Tucker compression of columns from a few of their fibres (3D cross-Tucker): the alternative the
+ * paper names for tensors too large to assemble whole for the HOSVD (end of Sec. II.B.1 and Sec. V,
+ * after the linear-time Tucker approximation of Oseledets, Savostyanov and Tyrtyshnikov 2008).
+ * Per tensor (column j, row block k), in FP64:
+ *   index sets I_g per mode; I_2, I_3 start as s0 indices floor((2l+1) n_g / (2 s0)), l < s0;
+ *   each sweep visits g = 1, 2, 3 with a < b the other modes:
+ *     F_g = the n_g x |I_a||I_b| mode-g fibres through every pair of I_a x I_b;
+ *     left singular pairs of F_g (two-pass Gram / Jacobi, as tucker_compress);
+ *     r_g = the smallest r with sum_{i>r} s_i^2 <= ((tol/4)^2 / 3) ||F_g||_F^2, capped at rmax
+ *           (the HOSVD rule on the sampled fibres at a quarter of the tolerance);
+ *     I_g = the first w_g = min(r_g + over, n_g, |I_a||I_b|) rows chosen by greedy pivoting
+ *           (Gaussian elimination taking the row of largest modulus) on the leading w_g
+ *           singular vectors;
+ *   after `sweeps` sweeps the factor U_g is the leading r_g singular vectors of the last F_g and
+ *   the core interpolates the tensor on the cross J_g = the first r_g pivots of I_g:
+ *     G = A[J_1, J_2, J_3] x1 M_1^-1 x2 M_2^-1 x3 M_3^-1,  M_g = U_g[J_g, :]  (r_g x r_g).
+ * The entries evaluated grow linearly with the grid's side; the error is not certified (unlike
+ * the HOSVD's bound) and is estimated on caller-chosen check fibres.
+ */
+typedef struct {
+  int32_t sweeps;  /* alternating sweeps, 1 .. 16 (0: 2) */
+  int32_t s0;      /* initial index-set size of modes 2 and 3, 1 .. 64 (0: 8) */
+  int32_t over;    /* pivots kept per mode beyond the rank, 0 .. 16 (a NULL params: 4) */
+  int32_t rmax;    /* largest rank per mode, 1 .. 64 (0: 64) */
+} zbc_cross_params;
+
+typedef struct {
+  int64_t entries;        /* tensor entries evaluated (fibres, cross, check fibres) */
+  double max_check_err;   /* largest relative Frobenius error on the check fibres (-1: none given) */
+} zbc_cross_stats;
+
+/*
+ * cross_tucker_compress -- the fibre cross on columns held in device memory (the fibres are read
+ * from them; the form that tests the method against the HOSVD of the same columns).
+ *   cols, ld, ncols, g, q, in_dt, tol, out : as tucker_compress (grid sizes even, <= 1024)
+ *   params      : NULL for the defaults {2, 8, 4, 64}
+ *   checks_host : host int32[nchecks][3], check fibre (g, i_a, i_b): the mode-g fibre through
+ *                 index i_a of mode a and i_b of mode b (a < b the other modes), the same for
+ *                 every tensor; nchecks in [0, 4096]
+ *   stats_host  : optional; max_rel_err is the largest check-fibre error (-1 without checks)
+ *   xstats_host : optional
+ * Synchronises the stream.  ZBC_EINVAL on bad arguments (message via zbc_last_error).
+ */
+int cross_tucker_compress(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
+                          double tol, const zbc_cross_params* params, const int32_t* checks_host, int nchecks,
+                          zbc_handle** out, zbc_compress_stats* stats_host, zbc_cross_stats* xstats_host,
+                          zbc_stream stream);
+
+/*
+ * cross_tucker_assemble -- the fibre cross with every entry evaluated from the Green's function
+ * (Eq. nNt / Eq. nKt, the same evaluation as vsie_assemble_columns_op): no column is ever
+ * assembled, so the memory is that of the fibres.
+ *   g, s, freq_hz, q (3 or 12), op, nq : as vsie_assemble_columns_op (grid sizes even, <= 1024)
+ *   cols_host   : host int32[ncols], segment indices in [0, s->m)
+ *   tol, params, checks_host, nchecks, out, stats_host, xstats_host : as cross_tucker_compress
+ * Synchronises the stream.
+ */
+int cross_tucker_assemble(const zbc_grid* g, const zbc_segments* s, double freq_hz, const int32_t* cols_host,
+                          int ncols, int q, zbc_operator op, int nq, double tol, const zbc_cross_params* params,
+                          const int32_t* checks_host, int nchecks, zbc_handle** out,
+                          zbc_compress_stats* stats_host, zbc_cross_stats* xstats_host, zbc_stream stream);
+
+/*
  * Rank-predictor MLP (no counterpart in the paper): 7 -> 64 -> 64 -> 64 -> 9 with ReLU, trained
  * on the GPU on log Tucker ranks.  Inputs per column (row-major, float32): segment centre / 0.1 m
  * (3), unit tangent (3), distance to the voxel box / 0.1 m (1).  Outputs: log(rank) of

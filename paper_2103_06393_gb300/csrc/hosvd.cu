@@ -18,45 +18,9 @@
 #include <cmath>
 #include <numeric>
 
-#include "zbc_internal.cuh"
+#include "hosvd.cuh"
 
 namespace zbc {
-
-// element (x, c) of a mode unfolding sits at x*sx + (c % d1)*e1 + (c / d1)*e2
-struct Unf {
-  int64_t sx, d1, e1, e2;
-  __device__ __forceinline__ int64_t at(int64_t x, int64_t c) const {
-    return x * sx + (c % d1) * e1 + (c / d1) * e2;
-  }
-};
-
-struct GramJob {
-  const void* A;  // tensor base
-  Unf u;
-  int64_t C;      // columns of the unfolding
-  int n;          // rows of the unfolding
-  double2* G;     // n x n
-};
-
-struct RotJob {    // out(x, c) = sum_i conj(V[i + ldv*x]) A(i, c),  x < r, i < n
-  const void* A;
-  Unf u;
-  int64_t C;
-  int n, r, ldv;
-  const double2* V;
-  double2* out;
-  Unf o;           // output placement of (x, c)
-};
-
-template <typename T>
-__device__ __forceinline__ double2 ld_z(const void* p, int64_t i) {
-  if constexpr (sizeof(T) == 16) {
-    return ((const double2*)p)[i];
-  } else {
-    float2 v = ((const float2*)p)[i];
-    return make_double2(v.x, v.y);
-  }
-}
 
 // ---------------------------------------------------------------------------------------------
 // Gram matrices G = A_(g) A_(g)^H, 32x32 output tiles, lower-triangle tiles only + mirror
@@ -163,15 +127,8 @@ __global__ void __launch_bounds__(256) rotate_kernel(const RotJob* jobs) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Hermitian Jacobi eigensolver, one CTA per matrix (n even, in global memory).  On return H is
-// diagonal (eigenvalues on the diagonal) and V holds the eigenvectors (columns).
+// Hermitian Jacobi eigensolver, one CTA per matrix (JacJob, hosvd.cuh)
 // ---------------------------------------------------------------------------------------------
-struct JacJob {
-  double2* H;
-  double2* V;
-  int n;
-};
-
 __global__ void __launch_bounds__(512) jacobi_kernel(const JacJob* jobs, int max_sweeps, int* sweeps_out) {
   const JacJob jb = jobs[blockIdx.x];
   const int n = jb.n;
@@ -294,14 +251,7 @@ __global__ void __launch_bounds__(256) norm2_kernel(const void* const* bases, in
   if (threadIdx.x == 0) partial[(int64_t)t * gridDim.x + blockIdx.x] = red[0];
 }
 
-// U[:, a] = V1 * W[:, ord[a]]  (n x r), FP64
-struct FacJob {
-  const double2* V1;
-  const double2* W;
-  const int* ord;
-  int n, r;
-  double2* U;
-};
+// U[:, a] = V1 * W[:, ord[a]]  (n x r), FP64 (FacJob, hosvd.cuh)
 __global__ void __launch_bounds__(256) factor_kernel(const FacJob* jobs) {
   const FacJob jb = jobs[blockIdx.y];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < jb.n * jb.r; e += gridDim.x * blockDim.x) {
@@ -313,38 +263,24 @@ __global__ void __launch_bounds__(256) factor_kernel(const FacJob* jobs) {
   }
 }
 
-// copy FP64 (src) -> complex64 (dst), several segments per job list
-struct CopyJob {
-  const double2* src;
-  float2* dst;
-  int64_t len;
-};
+// copy FP64 (src) -> complex64 (dst), several segments per job list (CopyJob, hosvd.cuh)
 __global__ void __launch_bounds__(256) pack_kernel(const CopyJob* jobs) {
   const CopyJob jb = jobs[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < jb.len; e += (int64_t)gridDim.x * blockDim.x)
     jb.dst[e] = make_float2((float)jb.src[e].x, (float)jb.src[e].y);
 }
 
+// launches of the FP64-operand forms for other translation units (hosvd.cuh)
+void launch_gram_f64(const GramJob* jobs, dim3 grid, cudaStream_t st) {
+  gram_kernel<double2><<<grid, 256, 0, st>>>(jobs);
+}
+void launch_rotate_f64(const RotJob* jobs, dim3 grid, cudaStream_t st) {
+  rotate_kernel<double2><<<grid, 256, 0, st>>>(jobs);
+}
+
 // ---------------------------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------------------------
-template <typename J>
-static int upload_jobs(DevBuf& buf, const std::vector<J>& jobs, cudaStream_t st) {
-  ZBC_TRY(buf.ensure(sizeof(J) * std::max<size_t>(1, jobs.size())));
-  ZBC_TRY_CUDA(cudaMemcpyAsync(buf.ptr, jobs.data(), sizeof(J) * jobs.size(), cudaMemcpyHostToDevice, st));
-  return ZBC_OK;
-}
-
-// Rank rule: smallest r >= 1 with sum_{i>r} lambda_i <= thr (lambda sorted descending, clamped >= 0)
-static int truncation_rank(const std::vector<double>& lam_desc, double thr) {
-  const int n = (int)lam_desc.size();
-  std::vector<double> tail(n + 1, 0.0);
-  for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + std::max(lam_desc[i], 0.0);
-  for (int r = 1; r <= n; ++r)
-    if (tail[r] <= thr) return r;
-  return n;
-}
-
 struct HosvdWork {
   DevBuf jobs_a, jobs_b, jobs_c, jobs_d;
   DevBuf H, V1, W, Bbuf, U, C1, C2, G, norm_part, ord, sweeps, base_ptrs;
@@ -1189,7 +1125,7 @@ int randomized_compress(const void* cols, int64_t ld, int ncols, int n1, int n2,
 using namespace zbc;
 
 // Append the compressed columns (ranks, packed pool) to *out (a new handle when *out is null).
-static int finish_compress(zbc_handle** out, const zbc_grid* g, int q, int ncols, const std::vector<int32_t>& ranks,
+int finish_compress(zbc_handle** out, const zbc_grid* g, int q, int ncols, const std::vector<int32_t>& ranks,
                            float2* pool, int64_t elems, zbc_compress_stats& stats, zbc_compress_stats* stats_host,
                            cudaStream_t stream) {
   zbc_handle* hh = *out;
@@ -1214,7 +1150,7 @@ static int finish_compress(zbc_handle** out, const zbc_grid* g, int q, int ncols
   return ZBC_OK;
 }
 
-static int check_compress_args(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
+int check_compress_args(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
                                double tol, zbc_handle** out) {
   ZBC_CHECK_ARG(cols && g && out, "tucker_compress: null argument");
   ZBC_CHECK_ARG(q >= 1 && q <= 12, "q must be in [1, 12]");

@@ -316,3 +316,15 @@ def mlp_init_params(seed: int) -> np.ndarray:
         parts.append(rng.uniform(-lim, lim, size=(fo, fi)).reshape(-1))
         parts.append(np.zeros(fo))
     return np.concatenate(parts).astype(np.float32)
+
+
+def cross_check_fibres(n, count: int, seed: int) -> np.ndarray:
+    """count check fibres (g, i_a, i_b) for the fibre cross: mode g uniform in {0, 1, 2}, then the
+    indices of the other two modes (a < b) uniform in their ranges; int32 (count, 3)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((count, 3), dtype=np.int32)
+    for c in range(count):
+        g = int(rng.integers(0, 3))
+        a, b = [m for m in range(3) if m != g]
+        out[c] = (g, rng.integers(0, n[a]), rng.integers(0, n[b]))
+    return out

@@ -50,6 +50,14 @@ class zbc_compress_stats(C.Structure):
                 ("max_rel_err", C.c_double)]
 
 
+class zbc_cross_params(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("s0", C.c_int32), ("over", C.c_int32), ("rmax", C.c_int32)]
+
+
+class zbc_cross_stats(C.Structure):
+    _fields_ = [("entries", C.c_int64), ("max_check_err", C.c_double)]
+
+
 class zbc_aca_stats(C.Structure):
     _fields_ = [("rank", C.c_int32), ("converged", C.c_int32), ("row_restarts", C.c_int32),
                 ("max_tucker_rank", C.c_int32), ("s2", C.c_double), ("last_term", C.c_double),
@@ -101,6 +109,12 @@ def lib():
             "zbc_rmatvec_noalloc": ([vp, vp, i64, i32, vp, i64, vp], i32),
             "zbc_product_status": ([vp, vp], i32),
             "zbc_tune": ([vp, i32, vp, vp], i32),
+            "cross_tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, C.POINTER(zbc_cross_params),
+                                       vp, i32, C.POINTER(vp), C.POINTER(zbc_compress_stats),
+                                       C.POINTER(zbc_cross_stats), vp], i32),
+            "cross_tucker_assemble": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, i32, i32, dbl,
+                                       C.POINTER(zbc_cross_params), vp, i32, C.POINTER(vp),
+                                       C.POINTER(zbc_compress_stats), C.POINTER(zbc_cross_stats), vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -320,6 +334,49 @@ def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle
     if append_to is not None:
         return append_to, st
     return Handle(h), st
+
+
+def _cross_args(params, checks):
+    prm = None
+    if params is not None:
+        prm = zbc_cross_params(**{k: int(v) for k, v in dict(params).items()})
+    chk = np.ascontiguousarray(np.zeros((0, 3)) if checks is None else checks, dtype=np.int32).reshape(-1, 3)
+    return prm, chk
+
+
+def cross_tucker_compress(cols, grid, tol: float, q=3, params=None, checks=None, append_to: Handle | None = None,
+                          stream=None):
+    """Tucker compression from fibres of columns held on the device (cols: column-major (ncols, ld)).
+    params: dict with sweeps / s0 / over / rmax (None: the defaults); checks: int array (n, 3) of
+    check fibres (g, i_a, i_b).  Returns (Handle, stats, cross stats)."""
+    import torch
+    g = grid_struct(grid)
+    dt = C128 if cols.dtype == torch.complex128 else C64
+    prm, chk = _cross_args(params, checks)
+    h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
+    st, xs = zbc_compress_stats(), zbc_cross_stats()
+    _check(lib().cross_tucker_compress(_ptr(cols), _ld(cols), cols.shape[0], C.byref(g), q, dt, tol,
+                                       C.byref(prm) if prm is not None else None,
+                                       chk.ctypes.data_as(C.c_void_p), chk.shape[0], C.byref(h), C.byref(st),
+                                       C.byref(xs), _stream(stream)))
+    return (append_to if append_to is not None else Handle(h)), st, xs
+
+
+def cross_tucker_assemble(grid, dsegs: DeviceSegments, freq_hz: float, cols, tol: float, q=3, op=OP_N, nq=1,
+                          params=None, checks=None, append_to: Handle | None = None, stream=None):
+    """Tucker compression from fibres whose entries are evaluated from the Green's function (no
+    column is assembled).  cols: host segment indices.  Returns (Handle, stats, cross stats)."""
+    g = grid_struct(grid)
+    s = dsegs.struct()
+    cidx = np.ascontiguousarray(np.atleast_1d(cols), dtype=np.int32)
+    prm, chk = _cross_args(params, checks)
+    h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
+    st, xs = zbc_compress_stats(), zbc_cross_stats()
+    _check(lib().cross_tucker_assemble(C.byref(g), C.byref(s), freq_hz, cidx.ctypes.data_as(C.c_void_p), cidx.size,
+                                       q, op, nq, tol, C.byref(prm) if prm is not None else None,
+                                       chk.ctypes.data_as(C.c_void_p), chk.shape[0], C.byref(h), C.byref(st),
+                                       C.byref(xs), _stream(stream)))
+    return (append_to if append_to is not None else Handle(h)), st, xs
 
 
 def aca_compress(grid, dsegs: DeviceSegments, freq_hz: float, tol: float, max_rank: int, mode=ACA_DENSE_U,
