@@ -554,6 +554,91 @@ def run_compression(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cross(args):
+    """Compression from fibres (3D cross-Tucker; end of Sec. II.B.1 and Sec. V) against column
+    assembly + truncated HOSVD, on columns of the bench workload (96^3 voxels, 2 mm, 298.2 MHz,
+    tol 1e-6): time per column, tensor entries evaluated per tensor against n_v, the check-fibre
+    error and the true error of both models against the assembled column (each handle decompressed
+    on the GPU as Z~ I with the FP32 forward product).  Prints one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_06393_gb300 import inputs, zbc
+
+    w = inputs.workload("precision")
+    g, s = w.grid, w.segments
+    tol = 1e-6
+    ncols = args.columns or 128
+    batch = min(64, ncols)
+    cols = (np.arange(ncols) * (s.m // ncols)).astype(np.int32)
+    ds = zbc.DeviceSegments(s)
+    chk = inputs.cross_check_fibres(g.shape, 24, seed=13)
+    nv = g.nv
+
+    def assemble(cb):
+        cd = torch.from_numpy(cb).cuda()
+        Z = zbc.colmajor(3 * nv, len(cb), torch.complex64)
+        zbc.vsie_assemble_columns(g, ds, w.freq_hz, cd, Z)
+        return Z
+
+    def true_err(h, Z, nb):
+        X = zbc.to_colmajor(np.eye(nb, dtype=np.complex64))
+        Y = zbc.colmajor(3 * nv, nb, torch.complex64)
+        zbc.zbc_matvec(h, X, Y, zbc.FP32_SIMT)
+        zbc.zbc_product_status(h)
+        d = (Y - Z).reshape(nb, 3, nv)
+        ref = Z.reshape(nb, 3, nv)
+        e = torch.linalg.vector_norm(d, dim=2) / torch.linalg.vector_norm(ref, dim=2)
+        return float(e.max())
+
+    # warm-up: one small batch each way (allocations, first launches)
+    Z = assemble(cols[:2])
+    zbc.tucker_compress(Z, g, tol)
+    zbc.cross_tucker_assemble(g, ds, w.freq_hz, cols[:2], tol, checks=chk)
+    torch.cuda.synchronize()
+    t_h = t_x = 0.0
+    eh = ex = echk = 0.0
+    entries = 0
+    rk_h, rk_x = [], []
+    for b0 in range(0, ncols, batch):
+        cb = cols[b0:b0 + batch]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Z = assemble(cb)
+        hh, _ = zbc.tucker_compress(Z, g, tol)
+        torch.cuda.synchronize()
+        t_h += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hx, _, xs = zbc.cross_tucker_assemble(g, ds, w.freq_hz, cb, tol, checks=chk)
+        torch.cuda.synchronize()
+        t_x += time.perf_counter() - t0
+        entries += xs.entries
+        echk = max(echk, xs.max_check_err)
+        eh = max(eh, true_err(hh, Z, len(cb)))
+        ex = max(ex, true_err(hx, Z, len(cb)))
+        rk_h.append(hh.export()[0].reshape(-1, 3))
+        rk_x.append(hx.export()[0].reshape(-1, 3))
+        del hh, hx, Z
+    rk_h, rk_x = np.concatenate(rk_h), np.concatenate(rk_x)
+    line = {
+        "metric": "Tucker compression time per column: from fibres (cross) vs assembly + HOSVD",
+        "value": 1e3 * t_x / ncols, "unit": "ms/column", "higher_is_better": False, "n_gpus": 1,
+        "data": "synthetic", "dtype": "f64 factorisation (HOSVD input c64)",
+        "config": {"workload": "precision: 96^3 voxels (2 mm), 8 loops x 128 segments, 298.2 MHz, tol 1e-6",
+                   "columns": ncols, "batch": batch, "check_fibres": len(chk),
+                   "cross": {"sweeps": 2, "s0": 8, "over": 4, "rmax": 64}},
+        "hosvd_ms_per_column": 1e3 * t_h / ncols,
+        "entries_per_tensor": entries / (3 * ncols),
+        "n_v": nv,
+        "max_check_err": echk,
+        "max_true_err": {"cross": ex, "hosvd": eh, "tol": tol},
+        "mean_rank": {"cross": float(rk_x.mean()), "hosvd": float(rk_h.mean())},
+        "max_rank_diff": int(np.abs(rk_x - rk_h).max()),
+        "column_bytes": {"assembled_c64": 3 * nv * 8, "fibres_f64": int(16 * entries / ncols)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batching(args):
     """Batching benchmark of the ACA workload (160 x 160 x 128 voxels at 1.5 mm, 16 loops x 256
     segments, ACA tol 1e-6, Tucker 3e-6): for p = 1 .. 128 right-hand sides, the tuned forward and
@@ -695,6 +780,8 @@ def main():
     ap.add_argument("--impl", default="zbc", choices=["zbc", "reference"])
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cross", action="store_true",
+                    help="compression from fibres (cross-Tucker) vs assembly + HOSVD instead of the products")
     ap.add_argument("--compression", action="store_true",
                     help="compression benchmark (HOSVD vs learned randomized Tucker) instead of the products")
     ap.add_argument("--batching", action="store_true",
@@ -704,6 +791,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.cross:
+        run_cross(args)
+        return
     if args.compression:
         run_compression(args)
     elif args.batching:

@@ -268,7 +268,8 @@ typedef struct {
 
 typedef struct {
   int64_t entries;        /* tensor entries evaluated (fibres, cross, check fibres) */
-  double max_check_err;   /* largest relative Frobenius error on the check fibres (-1: none given) */
+  double max_check_err;   /* largest estimated relative Frobenius error (-1: no check fibres):
+                             sqrt(mean over checks of n_a n_b ||fibre error||^2) / ||G||_F */
 } zbc_cross_stats;
 
 /*
@@ -279,7 +280,7 @@ typedef struct {
  *   checks_host : host int32[nchecks][3], check fibre (g, i_a, i_b): the mode-g fibre through
  *                 index i_a of mode a and i_b of mode b (a < b the other modes), the same for
  *                 every tensor; nchecks in [0, 4096]
- *   stats_host  : optional; max_rel_err is the largest check-fibre error (-1 without checks)
+ *   stats_host  : optional; max_rel_err is max_check_err below (an estimate, not a bound)
  *   xstats_host : optional
  * Synchronises the stream.  ZBC_EINVAL on bad arguments (message via zbc_last_error).
  */

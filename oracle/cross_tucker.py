@@ -117,19 +117,22 @@ def tucker_fibre(G, Us, g: int, ia: int, ib: int) -> np.ndarray:
 
 
 def check_error(entry, G, Us, n, checks) -> float:
-    """Relative Frobenius error of the Tucker model on the check fibres (g, ia, ib): 0 when the
-    fibres are all zero and so is the model on them."""
-    num = den = 0.0
+    """Relative Frobenius error of the Tucker model estimated from the check fibres (g, ia, ib):
+    a mode-g fibre drawn uniformly stands for all n_a n_b of them, so
+        e^2 = (1 / #checks) sum_checks n_a n_b ||A_fibre - model_fibre||^2
+    estimates ||A - model||_F^2, and the result is e / ||G||_F (= e / ||model||_F, the factors
+    being orthonormal).  0 when both are zero."""
+    num = 0.0
     for g, ia, ib in checks:
         a, b = OTHER[int(g)]
         idx = [None, None, None]
         idx[g] = np.arange(n[g])
         idx[a] = np.full(n[g], ia)
         idx[b] = np.full(n[g], ib)
-        ref = entry(idx[0], idx[1], idx[2])
-        d = ref - tucker_fibre(G, Us, int(g), int(ia), int(ib))
-        num += float(np.vdot(d, d).real)
-        den += float(np.vdot(ref, ref).real)
+        d = entry(idx[0], idx[1], idx[2]) - tucker_fibre(G, Us, int(g), int(ia), int(ib))
+        num += float(n[a]) * n[b] * float(np.vdot(d, d).real)
+    num /= len(checks)
+    den = float(np.vdot(G, G).real)
     if den == 0.0:
         return 0.0 if num == 0.0 else np.inf
     return float(np.sqrt(num / den))

@@ -17,7 +17,8 @@
 //   after the sweeps the core interpolates the tensor on the cross J_g (first r_g pivots):
 //     G = A[J_1, J_2, J_3] x1 M_1^-1 x2 M_2^-1 x3 M_3^-1,  M_g = U_g[J_g, :]
 //   (inverse_kernel: Gauss-Jordan with partial pivoting; the mode products reuse the HOSVD's rotate kernel);
-//   optional check fibres measure the relative error of the model (check_kernel).
+//   optional check fibres estimate the model's relative error (check_kernel): each stands for all
+//   fibres of its mode, e^2 = mean_c n_a n_b ||fibre error||^2, reported as e / ||G||_F.
 #include <cmath>
 #include <numeric>
 
@@ -614,15 +615,23 @@ static int cross_batch(const std::vector<XSrc>& src, const GreenGeom& Gg, double
     ZBC_TRY_CUDA(cudaGetLastError());
     count_launch();
     std::vector<double> part(2 * cj.size());
+    std::vector<double2> gh(ctot);
     ZBC_TRY_CUDA(cudaMemcpyAsync(part.data(), w.chk.ptr, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
+    ZBC_TRY_CUDA(cudaMemcpyAsync(gh.data(), Gc, sizeof(double2) * ctot, cudaMemcpyDeviceToHost, st));
     ZBC_TRY_CUDA(cudaStreamSynchronize(st));
+    // a uniformly drawn mode-g fibre stands for all n_a n_b of them:
+    //   e^2 = (1/#checks) sum_c n_a n_b ||fibre error||^2 estimates ||A - model||_F^2,
+    // relative to ||G||_F = ||model||_F (orthonormal factors)
     for (int t = 0; t < NT; ++t) {
-      double num = 0.0, den = 0.0;
+      double num = 0.0, gn = 0.0;
       for (int c = 0; c < nchk; ++c) {
-        num += part[2 * ((size_t)t * nchk + c)];
-        den += part[2 * ((size_t)t * nchk + c) + 1];
+        const int gm = checks[3 * c];
+        num += (double)n[other_a(gm)] * n[other_b(gm)] * part[2 * ((size_t)t * nchk + c)];
       }
-      const double e = den > 0.0 ? std::sqrt(num / den) : (num == 0.0 ? 0.0 : INFINITY);
+      num /= nchk;
+      const int64_t cs = (int64_t)rk[3 * t] * rk[3 * t + 1] * rk[3 * t + 2];
+      for (int64_t i = 0; i < cs; ++i) gn += gh[coff[t] + i].x * gh[coff[t] + i].x + gh[coff[t] + i].y * gh[coff[t] + i].y;
+      const double e = gn > 0.0 ? std::sqrt(num / gn) : (num == 0.0 ? 0.0 : INFINITY);
       *max_chk = std::max(*max_chk, e);
     }
   }

@@ -117,15 +117,20 @@ def test_green_source_indexes_the_column():
 
 
 def test_check_error_over_all_fibres_is_the_true_error():
-    # the check-fibre estimate taken over every mode-1 fibre is the Frobenius error itself
+    # the check-fibre estimate taken over every fibre of one mode is ||A - model||_F / ||model||_F
     w = inputs.scaled_workload("precision", (16, 12, 10), m=2)
     A = _green_tensor(w, 0, 1)
     G, Us, _ = xt.cross_tucker(xt.dense_source(A), A.shape, 1e-4)
-    checks = [(0, i2, i3) for i3 in range(10) for i2 in range(12)]
-    est = xt.check_error(xt.dense_source(A), G, Us, A.shape, checks)
-    assert est == pytest.approx(xt.error_vs_dense(A, G, Us), rel=1e-9)
-    # and a mode-2 and a mode-3 fibre agree with slicing the model
     M = tucker.reconstruct(G, Us)
+    true = np.linalg.norm(A - M) / np.linalg.norm(M)
+    for checks in ([(0, i2, i3) for i3 in range(10) for i2 in range(12)],
+                   [(2, i1, i2) for i2 in range(12) for i1 in range(16)]):
+        est = xt.check_error(xt.dense_source(A), G, Us, A.shape, checks)
+        assert est == pytest.approx(true, rel=1e-9)
+    # random fibres estimate it within a small factor
+    rnd = inputs.cross_check_fibres(A.shape, 64, seed=1)
+    assert 0.3 * true < xt.check_error(xt.dense_source(A), G, Us, A.shape, rnd) < 3 * true
+    # and a mode-2 and a mode-3 fibre agree with slicing the model
     assert np.allclose(xt.tucker_fibre(G, Us, 1, 3, 7), M[3, :, 7], rtol=0, atol=1e-15 * np.abs(M).max())
     assert np.allclose(xt.tucker_fibre(G, Us, 2, 5, 2), M[5, 2, :], rtol=0, atol=1e-15 * np.abs(M).max())
 
