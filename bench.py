@@ -554,6 +554,21 @@ def run_compression(args):
     print(json.dumps(line), flush=True)
 
 
+def cross_cpu_baseline(w, cols, tol, checks):
+    """The FP64 oracle's fibre cross (entries evaluated voxel by voxel from the Green's function,
+    as cross_tucker_assemble does) on a bounded sample of columns: ms per column."""
+    from oracle import cross_tucker as xt
+    g, s = w.grid, w.segments
+    t0 = time.perf_counter()
+    for e in cols:
+        for k in range(3):
+            src = xt.green_source(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, int(e), k,
+                                  mask_radius=g.mask_radius)
+            G, Us, _ = xt.cross_tucker(src, g.shape, tol)
+            xt.check_error(src, G, Us, g.shape, checks)
+    return 1e3 * (time.perf_counter() - t0) / len(cols)
+
+
 def run_cross(args):
     """Compression from fibres (3D cross-Tucker; end of Sec. II.B.1 and Sec. V) against column
     assembly + truncated HOSVD, on columns of the bench workload (96^3 voxels, 2 mm, 298.2 MHz,
@@ -636,6 +651,11 @@ def run_cross(args):
         "max_rank_diff": int(np.abs(rk_x - rk_h).max()),
         "column_bytes": {"assembled_c64": 3 * nv * 8, "fibres_f64": int(16 * entries / ncols)},
     }
+    if not args.no_cpu_baseline:
+        sample = cols[:: max(1, ncols // 4)][:4]
+        line["cpu_baseline"] = {"value": cross_cpu_baseline(w, sample, tol, chk), "unit": "ms/column",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{len(sample)} of the {ncols} columns (3 tensors each), same checks"}
     print(json.dumps(line), flush=True)
 
 
