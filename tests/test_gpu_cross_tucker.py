@@ -201,3 +201,20 @@ def test_bad_arguments_rejected():
     odd = inputs.Grid(15, 12, 10, g.h)
     with pytest.raises(zbc.ZbcError):
         zbc.cross_tucker_assemble(odd, ds, w.freq_hz, [0], 1e-5)
+
+
+def test_complex64_columns():
+    # the same columns stored complex64: ranks within 1 of the complex128 run, the same error level
+    w = inputs.scaled_workload("precision", (20, 16, 12), m=3)
+    g = w.grid
+    Z = _gpu_assemble(w)
+    Z64 = Z.to(torch.complex64)
+    h1, _, _ = zbc.cross_tucker_compress(Z, g, 1e-4)
+    h2, _, _ = zbc.cross_tucker_compress(Z64, g, 1e-4)
+    assert np.abs(_ranks(h1) - _ranks(h2)).max() <= 1
+    tens, _ = h2.tensors()
+    Zh = zbc.from_colmajor(Z)
+    for j in range(3):
+        for k in range(3):
+            A = tucker.fold(Zh[k * g.nv:(k + 1) * g.nv, j], g.shape)
+            assert _recon_err(A, tens[j][k]) <= 2e-4 + 1e-6
