@@ -202,23 +202,25 @@ def time_steps(fn, steps, flush, torch, stream):
 def mode1_gemm_flops(h, w, p, forward=False):
     """Real tensor-core flops of the mode-1 form's GEMMs, 3 fp16 products (hi.hi, hi.lo, lo.hi)
     per real MAC.  Adjoint: per group of 128 (column, rank) rows of one component, M = 128,
-    K = 2 n1p (n1 rounded up to 8), N = 2 n2 n3 P per pass of P <= 16 right-hand sides.
-    Forward: per block of 128 (i23, s) rows, M = 128, N = 2 n1f (n1 rounded up to 16),
-    K = 2 x the component's rows rounded up to chunks of 32."""
+    K = 2 n1p (n1 rounded up to 8, whatever the i1 tiling), N = 2 n2 n3 P per pass of
+    P in {1, 2, 4, 8, 16} right-hand sides.  Forward: per block of 128 (i23, s) rows and i1 tile
+    (ceil(n1 / 96) tiles of n1t = n1 / tiles rounded up to 16), M = 128, N = 2 n1t, K = 2 x the
+    component's rows rounded up to chunks of 32, passes of P in {4, 8, 16}."""
     g = w.grid
     ranks = h.export()[0]                      # (M, q, 3)
-    n2n3 = g.shape[1] * g.shape[2]
+    n1, n2n3 = g.shape[0], g.shape[1] * g.shape[2]
     if forward:
-        P = 16 if p > 8 else 8
+        P = 4 if p <= 4 else 8 if p <= 8 else 16
         nsc = -(-p // P)
         blocks = -(-n2n3 // (128 // P)) * nsc
         rows = sum(-(-int(ranks[:, k, 0].sum()) // 32) * 32 for k in range(ranks.shape[1]))
-        n1f = -(-g.shape[0] // 16) * 16
-        return 2.0 * 128 * (2 * n1f) * (2 * rows) * 3 * blocks
+        ntile1 = -(-n1 // 96)
+        n1t = -(-(-(-n1 // ntile1)) // 16) * 16
+        return 2.0 * 128 * (2 * n1t * ntile1) * (2 * rows) * 3 * blocks
     groups = sum(-(-int(ranks[:, k, 0].sum()) // 128) for k in range(ranks.shape[1]))
     P = 1 << max(0, (min(p, 16) - 1).bit_length())
     nsc = -(-p // P)
-    n1p = -(-g.shape[0] // 8) * 8
+    n1p = -(-n1 // 8) * 8                     # i1 tiles of 160 beyond 224 split K, not add to it
     return 2.0 * 128 * (2 * n1p) * (2 * n2n3 * P * nsc) * 3 * groups
 
 
