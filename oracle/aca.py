@@ -17,6 +17,12 @@ Readings where the paper is silent or garbled:
   * the new column is appended before the stopping test (r_c counts it);
   * the start row is row 0; if a residual row is exactly zero (a masked voxel),
     that row is marked used and the next unused row in index order is tried.
+
+Algorithm 3 takes two optional arguments used by the GPU parity tests:
+  * store=np.complex64 rounds every new Tucker tensor (core and factors) to complex64 before
+    it joins U, as a GPU handle stores them (reading R7); the arithmetic stays complex128;
+  * trace=True records, per iteration, the residual row r and column x the pivots were taken
+    from, so that a test can tell pivots decided by a clear margin from near-ties (reading R14).
 """
 import numpy as np
 
@@ -78,15 +84,32 @@ def aca_dense(get_row, get_col, m1: int, m2: int, tol: float, max_rank: int):
     return U, V, {"rank": U.shape[1], "pivots": pivots, "s2": s2, "converged": converged}
 
 
-def aca_tucker(get_row, get_col, n, q: int, m2: int, tol: float, max_rank: int, tucker_tol=None):
+def _stored(t, store):
+    """A new tensor (G, Us, info) as U keeps it: rounded to `store` (complex64) when given."""
+    if store is None:
+        return t
+    G, Us, info = t
+    rnd = lambda a: np.asarray(a).astype(store).astype(np.complex128)
+    return (rnd(G), [rnd(U) for U in Us], info)
+
+
+def aca_tucker(get_row, get_col, n, q: int, m2: int, tol: float, max_rank: int, tucker_tol=None,
+               store=None, trace=False, compress=None):
     """Algorithm 3: ACA of Z (q n_v x m2) with U assembled directly as Tucker tensors.
 
     Returns (tensors_u, V, info): tensors_u[l][k] = (G, [U1, U2, U3], hosvd_info).
+    store: None (complex128 tensors) or np.complex64 (tensors rounded as a GPU handle stores them).
+    trace: info["trace"][k] = {"r": row residual, "x": column residual, "nx", "ny", "s2"}.
+    compress: callable(A, tol) -> (G, [U1, U2, U3], info) used for U's tensors in place of the
+    truncated HOSVD (e.g. the randomized Tucker of oracle.randomized with its certified bound).
     """
+    if compress is None:
+        compress = tucker.hosvd
     n1, n2, n3 = n
     nv = n1 * n2 * n3
     m1 = q * nv
     ttol = 3.0 * tol if tucker_tol is None else tucker_tol
+    steps = []
     Ut = []
     V = np.zeros((m2, 0), dtype=np.complex128)
     used_r, used_c = set(), set()
@@ -123,13 +146,19 @@ def aca_tucker(get_row, get_col, n, q: int, m2: int, tol: float, max_rank: int, 
         if k > 0:
             uhx = products.rmatvec(Ut, n, x[:, None])[:, 0]
             s2 += 2.0 * np.sum((uhx * (V.conj().T @ y).conj()).real)
-        Ut.append([tucker.hosvd(tucker.fold(x[kk * nv:(kk + 1) * nv], n), ttol) for kk in range(q)])
+        Ut.append([_stored(compress(tucker.fold(x[kk * nv:(kk + 1) * nv], n), ttol), store)
+                   for kk in range(q)])
         V = np.concatenate([V, y[:, None]], axis=1)
         used_c.add(j)
         pivots.append((i, j))
+        if trace:
+            steps.append({"r": r, "x": x, "nx": nx, "ny": ny, "s2": s2})
         if nx * ny <= tol * np.sqrt(s2):
             converged = True
             break
         a = np.abs(x)
         i = _argmax_abs(a, used_r)
-    return Ut, V, {"rank": len(Ut), "pivots": pivots, "s2": s2, "converged": converged}
+    info = {"rank": len(Ut), "pivots": pivots, "s2": s2, "converged": converged}
+    if trace:
+        info["trace"] = steps
+    return Ut, V, info

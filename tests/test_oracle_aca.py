@@ -74,3 +74,32 @@ def test_masked_start_row_is_skipped():
     assert np.all(Z[0, :] == 0)            # corner voxel is masked
     U, V, info = aca.aca_dense(lambda i: Z[i, :], lambda j: Z[:, j], Z.shape[0], Z.shape[1], 1e-4, 48)
     assert info["pivots"][0][0] != 0
+
+
+def test_algorithm3_complex64_storage_and_trace():
+    """store=complex64 keeps tensors that are exactly complex64 values (reading R7), still tracks
+    the tolerance, and the trace's residuals are Algorithm 3's: x_k = Z[:, j_k] - U_{<k} V[j_k, <k]^H
+    on the stored tensors, and r_k = Z[i_k, :] - U_{<k}[i_k, :] V_{<k}^H by element-wise evaluation."""
+    g, Z = _green_case()
+    tol = 1e-5
+    Ut, Vt, info = aca.aca_tucker(lambda i: Z[i, :], lambda j: Z[:, j], g.shape, 3, Z.shape[1], tol, 48,
+                                  store=np.complex64, trace=True)
+    for col in Ut:
+        for G, Us, _ in col:
+            for a in [G] + list(Us):
+                assert np.array_equal(a, a.astype(np.complex64).astype(np.complex128))
+    Zt = products.matvec([[(G, Us) for G, Us, _ in col] for col in Ut], g.shape, Vt.conj().T)
+    assert np.linalg.norm(Z - Zt) / np.linalg.norm(Z) < 30 * tol
+    assert len(info["trace"]) == info["rank"]
+    tens = [[(G, Us) for G, Us, _ in col] for col in Ut]
+    for k, (i, j) in enumerate(info["pivots"]):
+        st = info["trace"][k]
+        x = Z[:, j].copy()
+        if k:
+            x -= products.matvec(tens[:k], g.shape, Vt[j, :k].conj()[:, None])[:, 0]
+        assert np.allclose(st["x"], x, rtol=0, atol=1e-12 * np.abs(Z).max())
+        r = Z[i, :].copy()
+        if k:
+            r -= np.array([tucker.reconstruct(*tens[l][i // g.nv]).reshape(-1, order="F")[i % g.nv]
+                           for l in range(k)]) @ Vt[:, :k].conj().T
+        assert np.allclose(st["r"], r, rtol=0, atol=1e-12 * np.abs(Z).max())

@@ -1,12 +1,14 @@
 """zbc_rmatvec_noalloc: the adjoint product for callers that cannot allocate device memory at
-call time (graph capture, fixed-memory loops).  It must agree with zbc_rmatvec on two calls in
-a row (the shared scratch array keeps the previous call's contents), work on ACA storage, and
-refuse, with a clear status, work that does not fit its fixed scratch or a handle whose
-decompression cache was never built.  Collected last so a failure here stops nothing else."""
+call time (a fixed memory budget, allocator hooks that must not re-enter the allocator).  On two
+calls in a row (the shared scratch array keeps the previous call's contents) it must agree with
+zbc_rmatvec and with the FP64 oracle's Algorithm 2 on the handle's own tensors, on plain and on
+ACA storage, and it must refuse, with a clear status, work that does not fit its fixed scratch
+or a handle whose decompression cache was never built.  Collected last so a failure here stops
+nothing else."""
 import numpy as np
 import pytest
 
-from oracle import greens, tucker
+from oracle import greens, products, tucker
 from paper_2103_06393_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -46,12 +48,20 @@ def test_noalloc_matches_rmatvec_twice(aca):
     zbc.zbc_rmatvec(h, Phi, ref, zbc.FP32_SIMT)        # also builds the decompression cache
     torch.cuda.synchronize()
     r = zbc.from_colmajor(ref)
+    tens, Vh = h.tensors()
+    Phih = zbc.from_colmajor(Phi).astype(np.complex128)
+    if aca:
+        ref_o = products.rmatvec_aca(tens, Vh.astype(np.complex128), g.shape, Phih)
+    else:
+        ref_o = products.rmatvec(tens, g.shape, Phih)
     for _ in range(2):
         out = zbc.colmajor(m, 5, torch.complex64)
         out.fill_(float("nan"))
         zbc.zbc_rmatvec_noalloc(h, Phi, out)
-        torch.cuda.synchronize()
-        assert _rel(zbc.from_colmajor(out), r) < RTOL
+        zbc.zbc_product_status(h)             # synchronises; raises if a device wait gave up
+        got = zbc.from_colmajor(out)
+        assert _rel(got, r) < RTOL            # the allocating entry point
+        assert _rel(got, ref_o) < RTOL        # the FP64 oracle (reading C11: per right-hand side)
 
 
 def test_noalloc_requires_built_cache():
