@@ -168,30 +168,60 @@ int vsie_assemble_columns_op(const zbc_grid* g, const zbc_segments* s, double fr
                              const int32_t* cols, int ncols, int q, zbc_operator op, int nq,
                              void* out, int64_t ld, zbc_dtype dt, zbc_stream stream);
 
+/* Rank-predictor MLP of the learned compression (declared with its calls below). */
+typedef struct zbc_mlp zbc_mlp;
+
+/*
+ * Inputs of the randomized Tucker methods of tucker_compress (no counterpart in the paper; see
+ * tucker_compress_randomized for the method).  Per (tensor t = j*q + k, mode g) the sketch width is
+ *   ZBC_RANDOMIZED_LEARNED : ceil(exp(mlp(features[j])[3k + g])) + oversample (q must be 3;
+ *                            zbc_rank_widths), the predictor's log-rank output for component k, mode g;
+ *   ZBC_RANDOMIZED_FIXED   : fixed_width for every tensor and mode;
+ * either way clamped to [2, min(n_g, lmax, 64)] and made even.
+ */
+typedef struct {
+  const zbc_mlp* mlp;       /* LEARNED: the trained predictor */
+  const float* features;    /* LEARNED: device float32, ncols x 7 row-major (zbc_mlp input layout) */
+  int32_t oversample;       /* LEARNED: added to the predicted rank, 0 .. 64 */
+  int32_t fixed_width;      /* FIXED: width of every (tensor, mode), >= 1 */
+  const void* sketch1;      /* device complex64 Gaussian test matrices Omega_g, N_g x lmax column-major */
+  const void* sketch2;      /*   (N_1 = n2 n3, N_2 = n1 n3, N_3 = n1 n2; unfolding order as in */
+  const void* sketch3;      /*   tucker_compress_randomized) */
+  int32_t lmax;             /* columns of each sketch, 2 .. 64 */
+} zbc_rank_model;
+
 /*
  * tucker_compress -- column-wise Tucker compression (Sec. III.A, Fig. 2; truncated HOSVD of
  * Sec. II.B.1 with De Lathauwer's bound).
- *   cols   : device, (q*n_v) x ncols column-major (ld >= q*n_v), dtype in_dt; q = 1 .. 12
- *            components per column (3: the point-matched piecewise-constant kernel; 12: a
- *            piecewise-linear basis, whose column assembly this library does not provide)
- *   tol    : per-tensor relative Frobenius tolerance; mode g keeps the smallest r_g with
- *            sum_{i>r_g} sigma_i^2 <= (tol^2/3) ||A||_F^2 (so ||A - A~||_F <= tol ||A||_F)
- *   method : ZBC_HOSVD (FP64 two-pass Gram + Jacobi eigensolver per unfolding), or one of the
- *            randomized methods (declared with the rank model, see zbc_mlp.h)
- *   out    : *out == NULL -> a new handle holding these ncols columns;
- *            *out != NULL -> the columns are appended to that handle (same grid and q)
- *   stats_host : optional (may be NULL)
- * Cores and factors are stored complex64.  Synchronises the stream (ranks size the storage).
+ *   cols     : device, (q*n_v) x ncols column-major (ld >= q*n_v), dtype in_dt; q = 1 .. 12
+ *              components per column (3: piecewise-constant basis; 12: the piecewise-linear basis
+ *              of vsie_assemble_columns_op)
+ *   tol      : per-tensor relative Frobenius tolerance; mode g keeps the smallest r_g with
+ *              sum_{i>r_g} sigma_i^2 <= (tol^2/3) ||A||_F^2 (so ||A - A~||_F <= tol ||A||_F)
+ *   method   : ZBC_HOSVD (FP64 two-pass Gram + Jacobi eigensolver per unfolding; model may be
+ *              NULL), or ZBC_RANDOMIZED_LEARNED / ZBC_RANDOMIZED_FIXED (the randomized range finder
+ *              of tucker_compress_randomized with the widths of `model`, and the HOSVD as the
+ *              fallback of every tensor whose widths fail the tolerance check); the error bound
+ *              tol ||A||_F holds for every method
+ *   model    : the randomized methods' inputs (zbc_rank_model); required by them, ignored by HOSVD
+ *   store_dt : storage type of cores and factors; only ZBC_C64 (the products compute in FP32 on
+ *              complex64 tensors; the paper stores complex128).  ZBC_C128 gives ZBC_EINVAL.
+ *   out      : *out == NULL -> a new handle holding these ncols columns;
+ *              *out != NULL -> the columns are appended to that handle (same grid and q)
+ *   stats_host : optional (may be NULL); n_fallback counts randomized tensors redone by HOSVD
+ * Synchronises the stream (ranks size the storage).  ZBC_EINVAL on bad arguments.
  */
 int tucker_compress(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q,
-                    zbc_dtype in_dt, double tol, zbc_tucker_method method,
-                    zbc_handle** out, zbc_compress_stats* stats_host, zbc_stream stream);
+                    zbc_dtype in_dt, double tol, zbc_tucker_method method, const zbc_rank_model* model,
+                    zbc_dtype store_dt, zbc_handle** out, zbc_compress_stats* stats_host, zbc_stream stream);
 
 typedef struct {
   int32_t rank;             /* r_c: columns of U and V */
   int32_t converged;        /* 1 if the stopping test |x||y| <= tol sqrt(s) was met */
   int32_t row_restarts;     /* all-zero residual rows skipped (masked voxels) */
   int32_t max_tucker_rank;  /* largest Tucker rank of the compressed U */
+  int32_t tucker_fallbacks; /* RANDOMIZED_FIXED: tensors of U redone by HOSVD */
+  int32_t reserved;
   double s2;                /* running estimate of ||U V^H||_F^2 */
   double last_term;         /* |x||y| of the last appended column */
   double max_tucker_err;    /* largest HOSVD error bound (relative) over the tensors of U */
@@ -206,7 +236,14 @@ typedef struct {
  *   max_rank   : upper bound on r_c
  *   mode       : ZBC_ACA_DENSE_U (dense U in HBM, complex128, compressed at the end) or
  *                ZBC_ACA_ALG3 (U never dense; each new column compressed at tucker_tol)
- *   tucker_tol : HOSVD tolerance for U's tensors; <= 0 selects 3*tol (Algorithm 3's choice)
+ *   tucker_tol : Tucker tolerance for U's tensors; <= 0 selects 3*tol (Algorithm 3's choice)
+ *   method     : how U's tensors are compressed: ZBC_HOSVD (the paper's truncated HOSVD; model may
+ *                be NULL) or ZBC_RANDOMIZED_FIXED (no counterpart in the paper: the certified
+ *                randomized range finder of tucker_compress with model->fixed_width for every
+ *                tensor and mode and the HOSVD as each failing tensor's fallback; the same
+ *                tucker_tol bound).  ZBC_RANDOMIZED_LEARNED is refused: U's columns are residual
+ *                columns, not single segments, so the rank predictor has no inputs for them.
+ *   model      : zbc_rank_model (sketches, lmax, fixed_width) for ZBC_RANDOMIZED_FIXED
  *   out        : new handle with U (Tucker, r_c columns) and V (m x r_c) -- Z = U V^H
  *   pivots_host: optional int32[2*max_rank]: (row, column) pivot pairs in order
  * Pivots, norms and the stopping test are FP64.  Ties pick the lowest index; rows and columns
@@ -214,8 +251,8 @@ typedef struct {
  * moves to the next unused row.  Synchronises the stream every iteration.
  */
 int aca_compress(const zbc_grid* g, const zbc_segments* s, double freq_hz, int q, double tol, int max_rank,
-                 zbc_aca_mode mode, double tucker_tol, zbc_handle** out, zbc_aca_stats* stats_host,
-                 int32_t* pivots_host, zbc_stream stream);
+                 zbc_aca_mode mode, double tucker_tol, zbc_tucker_method method, const zbc_rank_model* model,
+                 zbc_handle** out, zbc_aca_stats* stats_host, int32_t* pivots_host, zbc_stream stream);
 
 /*
  * tucker_compress_randomized -- column-wise Tucker compression by a fixed-width randomized range
@@ -313,7 +350,6 @@ int cross_tucker_assemble(const zbc_grid* g, const zbc_segments* s, double freq_
  * Parameter packing (float32): W1 (64x7 row-major [out][in]), b1 (64), W2 (64x64), b2, W3 (64x64),
  * b3, W4 (9x64), b4 (9) -- zbc_mlp_num_params() values.
  */
-typedef struct zbc_mlp zbc_mlp;
 int zbc_mlp_num_params(void);
 int zbc_mlp_create(const float* params_host, int n_params, zbc_mlp** out);
 int zbc_mlp_free(zbc_mlp* model);
@@ -363,17 +399,21 @@ int zbc_rmatvec(const zbc_handle* h, const void* Phi, int64_t ldphi, int p, void
 
 /*
  * zbc_rmatvec_noalloc -- Psi = Z^H Phi in FP32 on CUDA cores, like zbc_rmatvec with
- * ZBC_FP32_SIMT, but without allocating any memory.  The paper has no counterpart: this exists
- * for callers that cannot allocate device memory at the moment they need the product (inside a
- * CUDA graph capture, where cudaMalloc is not allowed; real-time or embedded loops whose memory
- * is fixed up front; allocator callbacks that must not re-enter the allocator).
+ * ZBC_FP32_SIMT, but without allocating any memory.  The paper has no counterpart.  It is for
+ * callers that cannot allocate device memory at the moment they need the product: real-time or
+ * embedded loops whose memory is fixed up front, allocator hooks that must not re-enter the
+ * allocator, and code running while a stream is being captured (cudaMalloc is not permitted
+ * there).  zbc_rmatvec keeps its partial sums in a per-handle buffer that grows on demand; this
+ * entry point uses a fixed array instead.
  *   - Partial sums live in one scratch array compiled into the library: 16 MiB of device memory
  *     on every GPU that loads the library, held until the process exits.  Calls whose q*M*p
  *     (+ M*p for ACA storage) complex64 values exceed it are rejected with ZBC_EINVAL.
  *   - The handle's decompression cache must already exist: call zbc_matvec or zbc_rmatvec on the
  *     handle once first (that call allocates); otherwise ZBC_EINVAL.
  *   - The scratch array's device address is looked up on the first call made on each device
- *     (with that device current); make that first call before any stream capture begins.
+ *     (with that device current) and kept for the life of the process; make that first call
+ *     before any stream capture begins, and do not use the library again on a device after
+ *     cudaDeviceReset (the kept address would be stale).
  *   - All calls share the array and it keeps the last call's contents; each call overwrites all
  *     it reads, so it needs no clearing, but calls that overlap on the GPU race on it.
  * Arguments are those of zbc_rmatvec.
@@ -396,13 +436,26 @@ int zbc_tune(zbc_handle* h, int p, zbc_stream stream, float* times_ms_host);
 
 /*
  * zbc_product_status -- device-side status of this handle's product kernels (zbc_matvec,
- * zbc_rmatvec, zbc_rmatvec_noalloc).  The products run asynchronously on `stream`; a product
- * kernel whose bounded wait (on its copy pipeline or on the tensor cores) gave up returns early
- * with its output incomplete and records that in a flag of the handle.  This call synchronises
- * `stream` and returns ZBC_ETIMEOUT if the flag is set (clearing it), else ZBC_OK.  The paper
- * has no counterpart.
+ * zbc_rmatvec, zbc_rmatvec_noalloc).  The products run asynchronously on `stream`, so their
+ * device-side failures are recorded in an error word of the handle:
+ *   - a product kernel whose bounded wait (on its copy pipeline or on the tensor cores) gave up
+ *     returns early with its output incomplete;
+ *   - a NaN or Inf read from X (forward products) or Phi (adjoint products) is noted as the
+ *     kernels read their inputs (the outputs then hold non-finite values; nothing stops).
+ * This call synchronises `stream`, clears the word and returns ZBC_ETIMEOUT if a wait gave up,
+ * else ZBC_ENAN if a non-finite input was seen, else ZBC_OK.  The paper has no counterpart.
  */
 int zbc_product_status(const zbc_handle* h, zbc_stream stream);
+
+/*
+ * zbc_test_wait_limit -- test hook for the bounded waits (no counterpart in the paper).  The next
+ * FP32 SIMT adjoint launch on this handle (zbc_rmatvec with ZBC_FP32_SIMT or zbc_rmatvec_noalloc)
+ * allows each consumer warp `polls` polls of the wait for its first stage (40,000,000 normally);
+ * polls = 0 makes that wait give up at once, so the launch takes its abort path (the copies
+ * already issued are still waited for, with the normal limit) and zbc_product_status reports
+ * ZBC_ETIMEOUT.  Later launches use the normal limit.
+ */
+int zbc_test_wait_limit(zbc_handle* h, uint32_t polls);
 
 /* Release a handle and its device memory (NULL is accepted). */
 int zbc_free(zbc_handle* h);
@@ -416,6 +469,15 @@ int zbc_get_info(const zbc_handle* h, zbc_info* info_host);
  * v = m * r_c * 8 (0 without ACA), full_equiv = q * n_v * m * 8.
  */
 int zbc_memory_bytes(const zbc_handle* h, int64_t* tucker_host, int64_t* v_host, int64_t* full_equiv_host);
+
+/*
+ * zbc_device_bytes -- device memory this handle holds now (no counterpart in the paper; beside
+ * zbc_memory_bytes' Table II model): pool = cores, factors, descriptors and V; caches = what the
+ * product calls build once and keep (the decompression cache W = G x2 U2 x3 U3 with tile-blocked
+ * U1, and the operands of the tensor-core forms); work = per-call workspaces grown so far
+ * (partial sums, transposed right-hand sides, fp16 copies of Phi).  Any pointer may be NULL.
+ */
+int zbc_device_bytes(const zbc_handle* h, int64_t* pool_host, int64_t* caches_host, int64_t* work_host);
 
 /*
  * Host import/export of the compressed storage (tests, checkpoints).

@@ -15,8 +15,11 @@
 // pivots; the norm update carries the conjugate that the Frobenius identity needs; the
 // start row is 0 and an all-zero residual row (a masked voxel) moves to the next unused row.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <set>
 
@@ -32,6 +35,29 @@ int assemble_columns_c128(const GreenGeom& G, const int32_t* cols, int ncols, do
 int hosvd_compress(const void* cols, int64_t ld, int ncols, int n1, int n2, int n3, int q, zbc_dtype dt, double tol,
                    std::vector<int32_t>& ranks, float2** pool, int64_t* elems, double* max_err, int batch_cols,
                    cudaStream_t st);
+int randomized_compress(const void* cols, int64_t ld, int ncols, int n1, int n2, int n3, int q, zbc_dtype dt,
+                        double tol, const int32_t* widths, const float2* const* sketch, int lmax,
+                        std::vector<int32_t>& ranks, float2** pool, int64_t* elems, zbc_compress_stats* stats,
+                        cudaStream_t st);
+
+// U's columns (complex128, ld N) in Tucker form: truncated HOSVD, or the fixed-width randomized
+// range finder with the HOSVD as the fallback of each tensor that fails its check
+static int compress_u(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, double tol,
+                      zbc_tucker_method method, const zbc_rank_model* model, int batch, std::vector<int32_t>& ranks,
+                      float2** pool, int64_t* elems, double* max_err, int* fallbacks, cudaStream_t st) {
+  if (method == ZBC_HOSVD)
+    return hosvd_compress(cols, ld, ncols, g->n1, g->n2, g->n3, q, ZBC_C128, tol, ranks, pool, elems, max_err, batch,
+                          st);
+  std::vector<int32_t> widths(3 * (size_t)ncols * q, model->fixed_width);
+  const float2* sk[3] = {(const float2*)model->sketch1, (const float2*)model->sketch2,
+                         (const float2*)model->sketch3};
+  zbc_compress_stats cs{};
+  ZBC_TRY(randomized_compress(cols, ld, ncols, g->n1, g->n2, g->n3, q, ZBC_C128, tol, widths.data(), sk, model->lmax,
+                              ranks, pool, elems, &cs, st));
+  *max_err = std::max(*max_err, cs.max_rel_err);
+  *fallbacks += cs.n_fallback;
+  return ZBC_OK;
+}
 
 __global__ void aca_row_kernel(GreenGeom G, int64_t v, int k, double2* __restrict__ out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -215,7 +241,8 @@ struct Dev {
 using namespace zbc;
 
 extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double freq_hz, int q, double tol, int max_rank,
-                            zbc_aca_mode mode, double tucker_tol, zbc_handle** out, zbc_aca_stats* stats,
+                            zbc_aca_mode mode, double tucker_tol, zbc_tucker_method method,
+                            const zbc_rank_model* model, zbc_handle** out, zbc_aca_stats* stats,
                             int32_t* pivots_host, zbc_stream st) {
   clear_error();
   ZBC_CHECK_ARG(g && s && out, "aca_compress: null argument");
@@ -225,6 +252,13 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
   ZBC_CHECK_ARG(s->m >= 1 && s->centre && s->tangent && s->length, "bad segments");
   ZBC_CHECK_ARG(tol > 0 && tol < 1 && max_rank >= 1, "bad tol or max_rank");
   ZBC_CHECK_ARG(mode == ZBC_ACA_DENSE_U || mode == ZBC_ACA_ALG3, "bad mode");
+  ZBC_CHECK_ARG(method == ZBC_HOSVD || method == ZBC_RANDOMIZED_FIXED,
+                "U's columns are compressed by ZBC_HOSVD or ZBC_RANDOMIZED_FIXED (they are residual columns of Z, "
+                "not single segments, so the rank predictor has no features for them)");
+  if (method == ZBC_RANDOMIZED_FIXED) {
+    ZBC_CHECK_ARG(model && model->sketch1 && model->sketch2 && model->sketch3, "RANDOMIZED_FIXED needs a rank model");
+    ZBC_CHECK_ARG(model->fixed_width >= 1 && model->lmax >= 2 && model->lmax <= 64, "bad fixed_width or lmax");
+  }
   if (!(tucker_tol > 0)) tucker_tol = 3.0 * tol;  // Algorithm 3 compresses U at 3 eps
   const GreenGeom G = make_green(g, s, freq_hz);
   const int m = s->m;
@@ -232,7 +266,7 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
   const int64_t N = (int64_t)q * nv;
   const int kmax = (int)std::min<int64_t>(std::min<int64_t>(N, m), max_rank);
 
-  Dev d_row, d_col, d_col32, d_tmp32, d_U, d_c, d_t, d_part, d_norm, d_max, d_used, d_cols;
+  Dev d_row, d_col, d_col32, d_tmp32, d_U, d_c, d_t, d_part, d_norm, d_normz, d_max, d_used, d_cols;
   ZBC_TRY(d_row.alloc(sizeof(double2) * m));
   ZBC_TRY(d_col.alloc(sizeof(double2) * N));
   ZBC_TRY(d_col32.alloc(sizeof(float2) * N));
@@ -242,6 +276,7 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
   const int NB = 512;
   ZBC_TRY(d_part.alloc(sizeof(double2) * (size_t)NB * kmax));
   ZBC_TRY(d_norm.alloc(sizeof(double) * NB));
+  ZBC_TRY(d_normz.alloc(sizeof(double) * NB));
   ZBC_TRY(d_max.alloc(sizeof(MaxIdx) * NB));
   ZBC_TRY(d_used.alloc(sizeof(int64_t) * (kmax + 1)));
   ZBC_TRY(d_cols.alloc(sizeof(int32_t)));
@@ -266,9 +301,12 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
   double s2 = 0.0, max_terr = 0.0, last = 0.0;
   int64_t i = 0;
   bool converged = false;
-  int restarts = 0;
+  int restarts = 0, fallbacks = 0;
   std::vector<double2> hrow(m), ht(kmax);
   int K = 0;
+  // ZBC_TRACE_ACA set: one line per iteration on stderr (progress of long compressions)
+  const bool trace = std::getenv("ZBC_TRACE_ACA") != nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
   for (int k = 0; k < kmax; ++k) {
     std::vector<cd> r(m);
     while (true) {
@@ -329,6 +367,12 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
     // column residual
     ZBC_TRY_CUDA(cudaMemcpyAsync(d_cols.p, &j, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     ZBC_TRY(assemble_columns_c128(G, (const int32_t*)d_cols.p, 1, (double2*)d_col.p, N, st));
+    // ||Z[:, j]||^2 (the scale of the terms the residual column is the difference of)
+    aca_norm_argmax_kernel<<<NB, 256, 0, st>>>((const double2*)d_col.p, N, nullptr, 0, (double*)d_normz.p,
+                                              (MaxIdx*)d_max.p);
+    count_launch();
+    std::vector<double> npz(NB);
+    ZBC_TRY_CUDA(cudaMemcpyAsync(npz.data(), d_normz.p, sizeof(double) * NB, cudaMemcpyDeviceToHost, st));
     std::vector<double2> c(K);
     for (int l = 0; l < K; ++l) {
       const cd cl = std::conj(V[l][j]);
@@ -380,8 +424,9 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
       }
     }
     ZBC_TRY_CUDA(cudaStreamSynchronize(st));
-    double nx2 = 0.0;
+    double nx2 = 0.0, nz2 = 0.0;
     for (int b = 0; b < NB; ++b) nx2 += np[b];
+    for (int b = 0; b < NB; ++b) nz2 += npz[b];
     double ny2 = 0.0;
     for (int e = 0; e < m; ++e) ny2 += std::norm(y[e]);
     const double nxy = std::sqrt(nx2) * std::sqrt(ny2);
@@ -407,11 +452,20 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
       std::vector<int32_t> rk;
       float2* pool = nullptr;
       int64_t elems = 0;
-      ZBC_TRY(hosvd_compress(d_col.p, N, 1, g->n1, g->n2, g->n3, q, ZBC_C128, tucker_tol, rk, &pool, &elems, &max_terr, 1,
-                             st));
+      ZBC_TRY(compress_u(d_col.p, N, 1, g, q, tucker_tol, method, model, 1, rk, &pool, &elems, &max_terr, &fallbacks,
+                         st));
       const int sa = handle_append(&hh->h, rk, pool, elems, 1, st);
       cudaFree(pool);
       if (sa != ZBC_OK) return sa;
+      if (trace) {
+        int rmax = 0;
+        for (int v : rk) rmax = std::max(rmax, v);
+        std::fprintf(stderr, "[aca] k %d i %lld j %d |x||y|/sqrt(s) %.3e |Z_j|/|x| %.3e max rank %d fallbacks %d %.1f ms\n",
+                     K, (long long)i, j, nxy / std::sqrt(std::max(s2, 1e-300)), std::sqrt(nz2 / std::max(nx2, 1e-300)),
+                     rmax, fallbacks,
+                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
+        std::fflush(stderr);
+      }
     }
     V.push_back(y);
     used_c.insert(j);
@@ -451,8 +505,8 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
     int64_t elems = 0;
     const int64_t per_col = (int64_t)q * nv * 16;
     const int batch = (int)std::max<int64_t>(1, std::min<int64_t>(K, ((int64_t)4 << 30) / per_col));
-    ZBC_TRY(hosvd_compress(d_U.p, N, K, g->n1, g->n2, g->n3, q, ZBC_C128, tucker_tol, rk, &pool, &elems, &max_terr, batch,
-                           st));
+    ZBC_TRY(compress_u(d_U.p, N, K, g, q, tucker_tol, method, model, batch, rk, &pool, &elems, &max_terr, &fallbacks,
+                       st));
     const int sa = handle_append(&hh->h, rk, pool, elems, K, st);
     cudaFree(pool);
     if (sa != ZBC_OK) return sa;
@@ -478,6 +532,7 @@ extern "C" int aca_compress(const zbc_grid* g, const zbc_segments* s, double fre
     stats->s2 = s2;
     stats->last_term = last;
     stats->max_tucker_err = max_terr;
+    stats->tucker_fallbacks = fallbacks;
   }
   if (pivots_host) std::copy(piv.begin(), piv.end(), pivots_host);
   *out = guard.release();

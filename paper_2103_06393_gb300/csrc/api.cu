@@ -177,6 +177,20 @@ extern "C" int zbc_get_info(const zbc_handle* hh, zbc_info* info) {
   return ZBC_OK;
 }
 
+extern "C" int zbc_device_bytes(const zbc_handle* hh, int64_t* pool, int64_t* caches, int64_t* work) {
+  clear_error();
+  ZBC_CHECK_ARG(hh, "zbc_device_bytes: null handle");
+  const Handle& h = hh->h;
+  if (pool)
+    *pool = (int64_t)(sizeof(float2) * h.pool_elems + sizeof(TensorDesc) * h.desc.size() +
+                      (h.has_v ? sizeof(float2) * (size_t)h.m * h.M : 0));
+  if (caches) *caches = cache_bytes(h.cache);
+  if (work)
+    *work = (int64_t)(h.work_partial.bytes + h.work_x.bytes + h.work_misc.bytes + h.work_xt.bytes +
+                      h.work_err.bytes + h.work_phi.bytes);
+  return ZBC_OK;
+}
+
 extern "C" int zbc_memory_bytes(const zbc_handle* hh, int64_t* tucker, int64_t* v, int64_t* full) {
   ZBC_CHECK_ARG(hh && tucker && v && full, "zbc_memory_bytes: null argument");
   const Handle& h = hh->h;

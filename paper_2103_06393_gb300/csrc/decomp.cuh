@@ -116,6 +116,7 @@ struct DecompCache {
   HalfDesc* d_half = nullptr;
   int kb1_max = 0;
   Mode1Cache* mode1 = nullptr;
+  int64_t bytes = 0;        // device bytes held (W, U1, descriptors, fp16 copies; not mode1's)
 };
 int build_decomp_cache(Handle& h, cudaStream_t st);
 int build_half_cache(Handle& h, cudaStream_t st);

@@ -105,6 +105,7 @@ int build_decomp_cache(Handle& h, cudaStream_t st) {
     set_error("decompression cache allocation failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
   }
+  c->bytes = (int64_t)(sizeof(float2) * std::max<int64_t>(1, off) + sizeof(CacheDesc) * T);
   const size_t sm = sizeof(float2) * r2max;
   for (int t0 = 0; t0 < T; t0 += 65535) {
     const int nt = std::min(65535, T - t0);
@@ -209,6 +210,7 @@ int build_half_cache(Handle& h, cudaStream_t st) {
   }
   cudaError_t e = cudaMalloc(&c->half, std::max<int64_t>(16, off));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_half, sizeof(HalfDesc) * std::max(1, T));
+  if (e == cudaSuccess) c->bytes += (int64_t)(std::max<int64_t>(16, off) + sizeof(HalfDesc) * std::max(1, T));
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_half, hd.data(), sizeof(HalfDesc) * T, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     for (int t0 = 0; t0 < T; t0 += 65535) {

@@ -284,6 +284,7 @@ void launch_rotate_f64(const RotJob* jobs, dim3 grid, cudaStream_t st) {
 struct HosvdWork {
   DevBuf jobs_a, jobs_b, jobs_c, jobs_d;
   DevBuf H, V1, W, Bbuf, U, C1, C2, G, norm_part, ord, sweeps, base_ptrs;
+  DevBuf skpart;  // partial sketches of the split sketch kernel
 };
 
 // Compress tensors t = 0..T-1 (tensor t = column t/q, component t%q) of one batch.
@@ -566,30 +567,37 @@ struct SketchJob {
 // Y(x, l) = sum_c A(x, c) Omega(c, l) in FP64.  (An FP32 sketch measured e^2 ~ 1e-13 ||A||^2 of
 // rounding noise on the 2 mm workloads, a sixth of the tol^2 = 1e-12 budget at tol 1e-6, which
 // inflated ranks; in FP64 the noise floor is far below the budget.)
+// Grid (x tiles of 32 rows, jobs, ksplit): with ksplit > 1 the unfolding's columns are cut into
+// ksplit ranges of whole 16-column chunks (so one tensor's sketch spreads over many SMs) and each
+// range's partial Y goes to part[(job * ksplit + z) * pstride + x + n l], summed in a fixed order
+// by sketch_reduce_kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) sketch_kernel(const SketchJob* jobs) {
+__global__ void __launch_bounds__(256) sketch_kernel(const SketchJob* jobs, int ksplit, double2* part,
+                                                     int64_t pstride) {
   const SketchJob jb = jobs[blockIdx.y];
   const int x0 = blockIdx.x * 32;
   if (x0 >= jb.n) return;
+  const int64_t chunk = ((jb.C + ksplit - 1) / ksplit + 15) / 16 * 16;
+  const int64_t cbeg = (int64_t)blockIdx.z * chunk, cend = min(jb.C, cbeg + chunk);
   __shared__ double2 sa[16][33];
   __shared__ double2 so[16][kWmax + 1];
   const int lx = threadIdx.x % 32, lg = threadIdx.x / 32;
   double2 acc[kWmax / 8];
 #pragma unroll
   for (int i = 0; i < kWmax / 8; ++i) acc[i] = make_double2(0.0, 0.0);
-  for (int64_t c0 = 0; c0 < jb.C; c0 += 16) {
+  for (int64_t c0 = cbeg; c0 < cend; c0 += 16) {
     for (int e = threadIdx.x; e < 16 * 32; e += 256) {
       const int cc = e / 32, xx = e % 32;
       const int64_t c = c0 + cc;
       double2 v = make_double2(0.0, 0.0);
-      if (c < jb.C && x0 + xx < jb.n) v = ld_z<T>(jb.A, jb.u.at(x0 + xx, c));
+      if (c < cend && x0 + xx < jb.n) v = ld_z<T>(jb.A, jb.u.at(x0 + xx, c));
       sa[cc][xx] = v;
     }
     for (int e = threadIdx.x; e < 16 * kWmax; e += 256) {
       const int cc = e / kWmax, l = e % kWmax;
       const int64_t c = c0 + cc;
       double2 v = make_double2(0.0, 0.0);
-      if (c < jb.C && l < jb.w) {
+      if (c < cend && l < jb.w) {
         const float2 o = jb.Om[c + jb.ldo * l];
         v = make_double2(o.x, o.y);
       }
@@ -604,10 +612,27 @@ __global__ void __launch_bounds__(256) sketch_kernel(const SketchJob* jobs) {
     }
     __syncthreads();
   }
+  double2* out = ksplit > 1 ? part + ((int64_t)blockIdx.y * ksplit + blockIdx.z) * pstride : jb.Y;
 #pragma unroll
   for (int i = 0; i < kWmax / 8; ++i) {
     const int l = lg + 8 * i;
-    if (x0 + lx < jb.n && l < jb.w) jb.Y[(x0 + lx) + (int64_t)jb.n * l] = acc[i];
+    if (x0 + lx < jb.n && l < jb.w) out[(x0 + lx) + (int64_t)jb.n * l] = acc[i];
+  }
+}
+
+// Y = sum over z of the ksplit partial sketches, in order z = 0, 1, ... (grid (x, jobs))
+__global__ void __launch_bounds__(256) sketch_reduce_kernel(const SketchJob* jobs, int ksplit,
+                                                            const double2* __restrict__ part, int64_t pstride) {
+  const SketchJob jb = jobs[blockIdx.y];
+  const int64_t ne = (int64_t)jb.n * jb.w;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int z = 0; z < ksplit; ++z) {
+      const double2 v = part[((int64_t)blockIdx.y * ksplit + z) * pstride + e];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    jb.Y[e] = s;
   }
 }
 
@@ -798,10 +823,22 @@ static int randomized_batch(const void* cols, int64_t ld, int ncols, int n1, int
     }
   ZBC_TRY(upload_jobs(w.jobs_a, sj, st));
   const int nmax = std::max(n1, std::max(n2, n3));
-  sketch_kernel<T><<<dim3(ceil_div(nmax, 32), (unsigned)sj.size()), 256, 0, st>>>((const SketchJob*)w.jobs_a.ptr);
+  // split the unfolding's columns when the x tiles of all jobs fill fewer than 4 CTAs per SM
+  const int64_t tiles = (int64_t)ceil_div(nmax, 32) * (int64_t)sj.size();
+  const int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, (4 * sm_count() + tiles - 1) / tiles));
+  const int64_t pstride = (int64_t)nmax * kWmax;
+  if (ksplit > 1) ZBC_TRY(w.skpart.ensure(sizeof(double2) * pstride * ksplit * sj.size()));
+  sketch_kernel<T><<<dim3(ceil_div(nmax, 32), (unsigned)sj.size(), ksplit), 256, 0, st>>>(
+      (const SketchJob*)w.jobs_a.ptr, ksplit, (double2*)w.skpart.ptr, pstride);
+  count_launch();
+  if (ksplit > 1) {
+    sketch_reduce_kernel<<<dim3(ceil_div(pstride, 256), (unsigned)sj.size()), 256, 0, st>>>(
+        (const SketchJob*)w.jobs_a.ptr, ksplit, (const double2*)w.skpart.ptr, pstride);
+    count_launch();
+  }
   ZBC_TRY(upload_jobs(w.jobs_b, qj, st));
   qr_kernel<<<(unsigned)qj.size(), 256, 0, st>>>((const QrJob*)w.jobs_b.ptr);
-  count_launch(2);
+  count_launch();
   ZBC_TRY_CUDA(cudaGetLastError());
   // C = A x1 Q1^H x2 Q2^H x3 Q3^H
   int w1m = 0, w2m = 0;
@@ -1192,25 +1229,30 @@ extern "C" int tucker_compress_randomized(const void* cols, int64_t ld, int ncol
 }
 
 extern "C" int tucker_compress(const void* cols, int64_t ld, int ncols, const zbc_grid* g, int q, zbc_dtype in_dt,
-                               double tol, zbc_tucker_method method, zbc_handle** out,
-                               zbc_compress_stats* stats_host, zbc_stream stream) {
+                               double tol, zbc_tucker_method method, const zbc_rank_model* model,
+                               zbc_dtype store_dt, zbc_handle** out, zbc_compress_stats* stats_host,
+                               zbc_stream stream) {
   clear_error();
-  ZBC_CHECK_ARG(method == ZBC_HOSVD,
-                "the randomized methods take widths and sketches: use tucker_compress_randomized");
-  ZBC_CHECK_ARG(cols && g && out, "tucker_compress: null argument");
-  ZBC_CHECK_ARG(q >= 1 && q <= 12, "q must be in [1, 12]");
-  ZBC_CHECK_ARG(g->n1 >= 2 && g->n2 >= 2 && g->n3 >= 2 && g->n1 <= 1024 && g->n2 <= 1024 && g->n3 <= 1024,
-                "grid sizes must be in [2, 1024]");
-  ZBC_CHECK_ARG(g->n1 % 2 == 0 && g->n2 % 2 == 0 && g->n3 % 2 == 0, "grid sizes must be even");
-  ZBC_CHECK_ARG(ncols >= 1, "ncols must be >= 1");
-  ZBC_CHECK_ARG(tol > 0 && tol < 1, "tol must be in (0, 1)");
-  ZBC_CHECK_ARG(in_dt == ZBC_C64 || in_dt == ZBC_C128, "bad dtype");
-  const int64_t nv = (int64_t)g->n1 * g->n2 * g->n3;
-  ZBC_CHECK_ARG(ld >= q * nv, "ld < q*n_v");
-  if (*out) {
-    const Handle& h0 = (*out)->h;
-    ZBC_CHECK_ARG(h0.n1 == g->n1 && h0.n2 == g->n2 && h0.n3 == g->n3 && h0.q == q && !h0.has_v,
-                  "append: grid/q mismatch or handle holds ACA storage");
+  ZBC_CHECK_ARG(method == ZBC_HOSVD || method == ZBC_RANDOMIZED_LEARNED || method == ZBC_RANDOMIZED_FIXED,
+                "unknown compression method %d", (int)method);
+  ZBC_CHECK_ARG(store_dt == ZBC_C64,
+                "only complex64 storage is provided (the product kernels compute in FP32 on complex64 tensors)");
+  ZBC_TRY(check_compress_args(cols, ld, ncols, g, q, in_dt, tol, out));
+  if (method != ZBC_HOSVD) {
+    // the randomized range finder with the model's widths (HOSVD fallback per tensor)
+    ZBC_CHECK_ARG(model, "the randomized methods need a zbc_rank_model");
+    ZBC_CHECK_ARG(model->sketch1 && model->sketch2 && model->sketch3, "zbc_rank_model: null sketch");
+    std::vector<int32_t> widths(3 * (size_t)ncols * q);
+    if (method == ZBC_RANDOMIZED_FIXED) {
+      ZBC_CHECK_ARG(model->fixed_width >= 1, "zbc_rank_model: fixed_width must be >= 1 (got %d)", model->fixed_width);
+      std::fill(widths.begin(), widths.end(), model->fixed_width);
+    } else {
+      ZBC_CHECK_ARG(model->mlp && model->features, "zbc_rank_model: the learned method needs mlp and features");
+      ZBC_CHECK_ARG(q == 3, "the rank predictor has outputs for q = 3 components only");
+      ZBC_TRY(zbc_rank_widths(model->mlp, model->features, ncols, g, model->oversample, widths.data(), stream));
+    }
+    return tucker_compress_randomized(cols, ld, ncols, g, q, in_dt, tol, widths.data(), model->sketch1,
+                                      model->sketch2, model->sketch3, model->lmax, out, stats_host, stream);
   }
   std::vector<int32_t> ranks;
   float2* pool = nullptr;
@@ -1218,6 +1260,7 @@ extern "C" int tucker_compress(const void* cols, int64_t ld, int ncols, const zb
   double max_err = 0.0;
   zbc_compress_stats stats{};
   // batch so that the FP64 rotated-unfolding buffer stays near 4 GB
+  const int64_t nv = (int64_t)g->n1 * g->n2 * g->n3;
   const int64_t per_col = (int64_t)q * nv * 16;
   int batch = (int)std::max<int64_t>(1, std::min<int64_t>(ncols, ((int64_t)4 << 30) / per_col));
   int s = hosvd_compress(cols, ld, ncols, g->n1, g->n2, g->n3, q, in_dt, tol, ranks, &pool, &elems, &max_err, batch,

@@ -1,19 +1,19 @@
 // zbc_rmatvec_noalloc: the FP32 adjoint product Psi = Z^H Phi with no memory allocation.
 //
-// Some callers cannot allocate device memory when they need the product: code running while a
-// CUDA graph is being captured (cudaMalloc is not capturable), real-time loops and embedded
-// users whose memory is fixed up front, or callers inside a custom allocator that must not
-// re-enter it.  zbc_rmatvec keeps its partial sums in a per-handle buffer that grows on demand;
-// this variant instead uses one fixed scratch array compiled into the library
-// (kScratchBytes = 16 MiB of device memory, held by every GPU that loads the library until
-// the process exits).
+// Some callers cannot allocate device memory when they need the product: real-time loops and
+// embedded users whose memory is fixed up front, allocator hooks that must not re-enter the
+// allocator, and code running while a stream is captured (cudaMalloc is not permitted there).
+// zbc_rmatvec keeps its partial sums in a per-handle buffer that grows on demand; this variant
+// instead uses one fixed scratch array compiled into the library (kScratchBytes = 16 MiB of
+// device memory, held by every GPU that loads the library until the process exits).
 //
 // The array's host-side name is only a stand-in: its device address is taken once per device
-// with cudaGetSymbolAddress, on the first call made while that device is current.  That first
-// call should therefore happen before any stream capture begins.  Every call shares the array
-// and it keeps the last call's contents; each call overwrites every entry it reads, so nothing
-// needs clearing, but two calls that overlap on the GPU (different streams, different threads)
-// race on it.
+// with cudaGetSymbolAddress, on the first call made while that device is current, and kept for
+// the life of the process (a cudaDeviceReset would make it stale).  That first call should
+// therefore happen before any stream capture begins.  Every call shares the array and it keeps
+// the last call's contents; each call overwrites every entry it reads, so nothing needs
+// clearing, but two calls that overlap on the GPU (different streams, different threads) race
+// on it.
 #include <mutex>
 
 #include "zbc_internal.cuh"

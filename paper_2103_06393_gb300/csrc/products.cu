@@ -175,6 +175,18 @@ extern "C" int zbc_product_status(const zbc_handle* hh, zbc_stream stream) {
   ZBC_TRY_CUDA(cudaMemcpy(&flag, h.work_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
   if (!flag) return ZBC_OK;
   ZBC_TRY_CUDA(cudaMemset(h.work_err.ptr, 0, sizeof(int)));
-  set_error("a product kernel gave up a bounded device wait; its output is incomplete");
-  return ZBC_ETIMEOUT;
+  if (flag & kErrTimeout) {
+    set_error("a product kernel gave up a bounded device wait; its output is incomplete%s",
+              (flag & kErrNonFinite) ? " (and a NaN or Inf was read from X or Phi)" : "");
+    return ZBC_ETIMEOUT;
+  }
+  set_error("a NaN or Inf was read from X or Phi; the products' outputs are not finite");
+  return ZBC_ENAN;
+}
+
+extern "C" int zbc_test_wait_limit(zbc_handle* hh, uint32_t polls) {
+  clear_error();
+  ZBC_CHECK_ARG(hh, "zbc_test_wait_limit: null handle");
+  hh->h.test_first_wait = polls;
+  return ZBC_OK;
 }

@@ -82,6 +82,11 @@ __global__ void __launch_bounds__(128) mode1_build_kernel(const float2* __restri
   }
 }
 
+int64_t cache_bytes(const DecompCache* c) {
+  if (!c) return 0;
+  return c->bytes + (c->mode1 ? c->mode1->bytes : 0);
+}
+
 int build_mode1_cache(Handle& h, cudaStream_t st) {
   ZBC_TRY(build_decomp_cache(h, st));
   DecompCache& dc = *h.cache;
@@ -125,6 +130,9 @@ int build_mode1_cache(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&c->kg_k, sizeof(int) * KG);
   if (e == cudaSuccess) e = cudaMalloc(&c->colrows, sizeof(int2) * colrows.size());
   if (e == cudaSuccess) e = cudaMalloc(&c->rowsrc, sizeof(int4) * src.size());
+  if (e == cudaSuccess)
+    c->bytes = (int64_t)(abytes + sizeof(Mode1Row) * rows.size() + sizeof(int) * KG + sizeof(int2) * colrows.size() +
+                         sizeof(int4) * src.size());
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->rows, rows.data(), sizeof(Mode1Row) * rows.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->kg_k, kg_k.data(), sizeof(int) * KG, cudaMemcpyHostToDevice, st);
@@ -173,7 +181,7 @@ struct M1Geo {
 // row per chunk).
 __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict__ Phi, int64_t ldphi, int p,
                                                         int64_t nv, M1Geo G, uint32_t* __restrict__ Bop,
-                                                        int* __restrict__ Eblk) {
+                                                        int* __restrict__ Eblk, int* __restrict__ err) {
   const int nb = blockIdx.x, sc = blockIdx.y, k = blockIdx.z;
   const int KB4 = G.KC / 4;
   const int npiece = G.NB * G.nkc * KB4;
@@ -203,12 +211,15 @@ __global__ void __launch_bounds__(256) phi_split_kernel(const float2* __restrict
     decode(pi, c, n, kc);
     if ((n & 1) || !source(n, c, kc, i1, off)) continue;
     float mx = 0.f;
+    bool finite = true;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (i1 + i < G.n1) {
         const float2 v = Phi[off + i1 + i];
+        finite = finite && isfinite(v.x) && isfinite(v.y);
         mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
+    if (!finite) atomicOr(err, kErrNonFinite);  // the exponents below then mean nothing
     if (mx > 0.f) atomicMax(&smax[(n >> 1) % G.P], __float_as_uint(mx));
   }
   __syncthreads();
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(M1Shape<NB>::threads, 1) rmatvec_mode1_kernel(
   }
   tc::fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicExch(prm.err, 1);
+  if (threadIdx.x == 0 && abort_flag) atomicOr(prm.err, kErrTimeout);
   if (warp == 0) tc::tmem_dealloc(tbase, prm.tcols);
 }
 
@@ -629,7 +640,8 @@ static int rmatvec_mode1_p(Handle& h, const float2* Phi, int64_t ldphi, int p, f
   ZBC_TRY(h.work_partial.ensure(sizeof(float2) * (size_t)nslots * rows_all * ppad));
   uint32_t* Bop = (uint32_t*)h.work_phi.ptr;
   int* Eblk = (int*)((unsigned char*)h.work_phi.ptr + bop_bytes);
-  phi_split_kernel<<<dim3(G.NBT, G.nsc, h.q), 256, 0, st>>>(Phi, ldphi, p, h.nv(), G, Bop, Eblk);
+  phi_split_kernel<<<dim3(G.NBT, G.nsc, h.q), 256, 0, st>>>(Phi, ldphi, p, h.nv(), G, Bop, Eblk,
+                                                            (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   M1Params prm;

@@ -176,6 +176,9 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&mc.chunkinfo, sizeof(int2) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&mc.jtab, (size_t)NC * kFwdChunk);
   if (e == cudaSuccess) e = cudaMalloc(&mc.d_chbase, sizeof(int) * (q + 1));
+  if (e == cudaSuccess)
+    mc.bytes += (int64_t)(sizeof(uint32_t) * bwords + sizeof(float2) * wc_elems + sizeof(int) * (size_t)q * n23p +
+                          sizeof(int2) * NC + (size_t)NC * kFwdChunk + sizeof(int) * (q + 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_row0, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_nr, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_ck, sizeof(int) * NC);
@@ -223,15 +226,19 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
 // ex[s] = exponent of max_j |Re|, |Im| of X[j, s]; XT[sc][j][P] = X[j, sc P + s] 2^-ex (zero for
 // s >= p).  One CTA per padded right-hand side.
 __global__ void __launch_bounds__(256) m1f_x_kernel(const float2* __restrict__ X, int64_t ldx, int M, int p, int P,
-                                                    float2* __restrict__ XT, int* __restrict__ ex) {
+                                                    float2* __restrict__ XT, int* __restrict__ ex,
+                                                    int* __restrict__ err) {
   const int sg = blockIdx.x, sc = sg / P, sl = sg % P;
   __shared__ float wmax[8];
   float mx = 0.f;
+  bool finite = true;
   if (sg < p)
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
       const float2 v = X[j + ldx * sg];
+      finite = finite && isfinite(v.x) && isfinite(v.y);
       mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
+  if (!finite) atomicOr(err, kErrNonFinite);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
@@ -512,7 +519,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) matvec_mode1_kernel(const FwdP
   }
   tc::fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicExch(prm.err, 1);
+  if (threadIdx.x == 0 && abort_flag) atomicOr(prm.err, kErrTimeout);
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
@@ -551,7 +558,7 @@ static int matvec_mode1_p(Handle& h, const float2* X, int64_t ldx, int p, float2
   float2* XT = (float2*)h.work_xt.ptr;
   float2* XE = XT + xt_elems;
   int* ex = (int*)(XE + xe_elems);
-  m1f_x_kernel<<<prm.nsc * P, 256, 0, st>>>(X, ldx, h.M, p, P, XT, ex);
+  m1f_x_kernel<<<prm.nsc * P, 256, 0, st>>>(X, ldx, h.M, p, P, XT, ex, (int*)h.work_err.ptr);
   m1f_xe_kernel<<<ceil_div((int64_t)xe_elems, 256), 256, 0, st>>>(XT, mc.chunkinfo, mc.jtab, h.M, prm.NC, P, prm.nsc,
                                                                    XE);
   ZBC_TRY_CUDA(cudaGetLastError());

@@ -52,11 +52,13 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
 
 // X^T[j][s] = X[j, s] for s < p, zero up to the row stride pst (a whole number of s-chunks)
 __global__ void __launch_bounds__(256) transpose_x_kernel(const float2* __restrict__ X, int64_t ldx, int M, int p,
-                                                          int pst, float2* __restrict__ XT) {
+                                                          int pst, float2* __restrict__ XT, int* __restrict__ err) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)M * pst) return;
   const int j = (int)(e / pst), s = (int)(e % pst);
-  XT[e] = s < p ? X[j + ldx * s] : make_float2(0.f, 0.f);
+  const float2 v = s < p ? X[j + ldx * s] : make_float2(0.f, 0.f);
+  if (!(isfinite(v.x) && isfinite(v.y))) atomicOr(err, kErrNonFinite);
+  XT[e] = v;
 }
 
 int transpose_rhs(Handle& h, const float2* X, int64_t ldx, int p, int chunk, const float2** XT, int* pst,
@@ -64,7 +66,8 @@ int transpose_rhs(Handle& h, const float2* X, int64_t ldx, int p, int chunk, con
   *pst = (ceil_div(p, chunk) * chunk + 1) / 2 * 2;
   ZBC_TRY(h.work_xt.ensure(sizeof(float2) * (size_t)h.M * *pst));
   float2* xt = (float2*)h.work_xt.ptr;
-  transpose_x_kernel<<<ceil_div((int64_t)h.M * *pst, 256), 256, 0, st>>>(X, ldx, h.M, p, *pst, xt);
+  transpose_x_kernel<<<ceil_div((int64_t)h.M * *pst, 256), 256, 0, st>>>(X, ldx, h.M, p, *pst, xt,
+                                                                          (int*)h.work_err.ptr);
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   *XT = xt;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && abort_flag) atomicOr(err, kErrTimeout);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -185,11 +188,24 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
 // reduce-scatter into the stage's red[warp][NV]; the producer warp adds the warps' values in
 // warp order into pacc[j][NV] (fixed order: results are reproducible) before it reuses the stage.
 // ---------------------------------------------------------------------------------------------
+// Bounded wait on an mbarrier phase that also gives up once another warp of the CTA has set
+// *abort_flag (checked between slices of 1024 polls; kWaitPolls polls in all).
+__device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t done = 0; done < kWaitPolls; done += 1024u) {
+    if (*abort_flag) return false;
+    if (tc::mbar_wait(mbar, parity, 1024u)) return true;
+  }
+  return false;
+}
+
+// first_wait: polls allowed to each consumer warp's wait for its first stage (kWaitPolls, or the
+// test limit of zbc_test_wait_limit, which makes that wait give up and the CTA abort).  Non-finite
+// Phi values set kErrNonFinite in err.
 template <int PS, int NT>
 __global__ void __launch_bounds__(32 * (NT + 1), 1)
     rmatvec_simt_kernel(const float2* __restrict__ cache, const CacheDesc* __restrict__ cdesc, Geo g, int q, int M,
                         int MJ, StageLayout SL, int S, const float2* __restrict__ Phi, int64_t ldphi, int p,
-                        float2* __restrict__ partial, int* __restrict__ err) {
+                        float2* __restrict__ partial, int* __restrict__ err, uint32_t first_wait) {
   constexpr int NV = 2 * PS;
   constexpr int NH = PS > 8 ? 2 : 1;  // halves of the right-hand sides
   constexpr int PSH = PS / NH, NVH = 2 * PSH;
@@ -237,7 +253,7 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
       const int st = c % S;
       if (c >= S) {
         bool bad = abort_flag != 0;
-        if (!bad) bad = !tc::mbar_wait(&empty[st], ((c / S) - 1) & 1);
+        if (!bad) bad = !wait_or_abort(&empty[st], ((c / S) - 1) & 1, &abort_flag);
         if (__any_sync(0xffffffffu, bad)) {
           if (lane == 0) abort_flag = 1;
           break;
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
     if (!__any_sync(0xffffffffu, abort_flag != 0)) {
       for (int c = std::max(0, nitems - S); c < nitems; ++c) {
         bool bad = abort_flag != 0;
-        if (!bad) bad = !tc::mbar_wait(&empty[c % S], (c / S) & 1);
+        if (!bad) bad = !wait_or_abort(&empty[c % S], (c / S) & 1, &abort_flag);
         if (__any_sync(0xffffffffu, bad)) {
           if (lane == 0) abort_flag = 1;
           break;
@@ -277,6 +293,7 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
     int t = (int)(c0 / (nj > 0 ? nj : 1)), jl = (int)(c0 % (nj > 0 ? nj : 1));
     int tcur = -1, il = 0, u0 = 0;
     bool okl[kUQ];
+    bool finite = true;
     float2 ph[kUQ][PS];
     for (int c = 0; c < nitems; ++c) {
       const int st = c % S;
@@ -294,8 +311,10 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
           okl[l] = ok && (u0 + l) < g.NU && i2 < g.n2;
           const int64_t v = i1 + (int64_t)g.n1 * (i2 + (int64_t)g.n2 * i3);
 #pragma unroll
-          for (int i = 0; i < PS; ++i)
+          for (int i = 0; i < PS; ++i) {
             ph[l][i] = (okl[l] && s0 + i < p) ? Phi[k * nv + v + ldphi * (s0 + i)] : make_float2(0.f, 0.f);
+            finite = finite && isfinite(ph[l][i].x) && isfinite(ph[l][i].y);
+          }
         }
       }
       if (++jl == nj) {
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
       }
       // warp-uniform decisions: the warp shuffles below need every lane
       if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], (c / S) & 1))) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], (c / S) & 1, c == 0 ? first_wait : kWaitPolls))) {
         if (lane == 0) abort_flag = 1;
         break;
       }
@@ -336,9 +355,10 @@ __global__ void __launch_bounds__(32 * (NT + 1), 1)
       __syncwarp();
       if (lane == 0) mbar_arrive1(&empty[st]);
     }
+    if (!finite) atomicOr(err, kErrNonFinite);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && abort_flag) atomicOr(err, kErrTimeout);
   float2* out = partial + (int64_t)(blockIdx.x * q + k) * M * p;
   for (int e = threadIdx.x; e < nj * PS; e += blockDim.x) {
     const int j = e % nj, i = e / nj;
@@ -466,7 +486,9 @@ static int launch_rmatvec(Handle& h, const float2* Phi, int64_t ldphi, int p, fl
   ZBC_TRY((set_smem_limit<rmatvec_simt_kernel<PS, NT>>((int)kSmemBudget)));
   dim3 grid(G, h.q * jblocks, schunks);
   rmatvec_simt_kernel<PS, NT><<<grid, 32 * (g.ntask + 1), sm, st>>>(h.cache->data, h.cache->d_desc, g, h.q, h.M, MJ, SL,
-                                                                S, Phi, ldphi, p, scratch, (int*)h.work_err.ptr);
+                                                                S, Phi, ldphi, p, scratch, (int*)h.work_err.ptr,
+                                                                h.test_first_wait);
+  h.test_first_wait = kWaitPolls;  // a test limit applies to one launch
   ZBC_TRY_CUDA(cudaGetLastError());
   count_launch();
   return reduce_partials(scratch, G * h.q, h.M, p, out, ldo, st);

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && abort_flag) atomicOr(err, kErrTimeout);
   if (warp == 0) tc::tmem_dealloc(tbase, L.tmem_cols);
 }
 

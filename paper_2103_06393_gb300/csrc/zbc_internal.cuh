@@ -68,8 +68,16 @@ struct TensorDesc {
   float scale_log2;   // floor(log2 ||G||_F), used for the per-column scaling of the fp16 path
 };
 
+// bits of a handle's device error word (work_err), read and cleared by zbc_product_status
+constexpr int kErrTimeout = 1;    // a bounded wait gave up; the kernel's output is incomplete
+constexpr int kErrNonFinite = 2;  // a NaN or Inf was read from X or Phi
+
+// polls of the bounded mbarrier waits in the product kernels
+constexpr uint32_t kWaitPolls = 40000000u;
+
 struct DecompCache;  // W = G x2 U2 x3 U3 and tile-blocked U1 per tensor, built lazily (decomp_cache.cu)
 void cache_release(DecompCache* c);
+int64_t cache_bytes(const DecompCache* c);  // device bytes held by a cache (0 for null)
 
 struct Handle {
   int n1 = 0, n2 = 0, n3 = 0, q = 0;
@@ -88,7 +96,7 @@ struct Handle {
   DevBuf work_x;         // X' = V^H X (ACA), scaled operands
   DevBuf work_misc;
   DevBuf work_xt;        // X^T of the forward products (s-chunk padded rows)
-  DevBuf work_err;       // int: set by a product kernel whose bounded wait gave up
+  DevBuf work_err;       // int: error bits kErrTimeout / kErrNonFinite set by the product kernels
   DevBuf work_phi;       // mode-1 adjoint: fp16 operand blocks of Phi and their exponents
   DecompCache* cache = nullptr;
   int cache_r = 0;                 // largest r1 rounded up to 2 (cache row stride bound)
@@ -98,6 +106,9 @@ struct Handle {
   int8_t tune_fwd_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
   int8_t tune_adj_warps[kPClasses] = {0, 0, 0, 0, 0, 0, 0, 0};
   int8_t tune_adj_prec[kPClasses] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  // polls allowed to the first stage wait of each consumer warp of the next FP32 SIMT adjoint
+  // launch (zbc_test_wait_limit; reset after that launch); kWaitPolls otherwise
+  uint32_t test_first_wait = kWaitPolls;
   ~Handle();
   int64_t nv() const { return (int64_t)n1 * n2 * n3; }
   int upload();          // copy desc to device (pool already on device)

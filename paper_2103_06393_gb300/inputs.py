@@ -275,6 +275,20 @@ def cn01(shape, seed: int, dtype=np.complex128) -> np.ndarray:
     return np.asfortranarray(a.astype(dtype))
 
 
+def cn01_columns_c64(rows: int, cols: int, seed: int) -> np.ndarray:
+    """CN(0,1) complex64 matrix (column-major) generated column by column, column s from its own
+    stream default_rng([seed, s]) in float32: the right-hand sides of the largest workloads
+    (tens of GB) without a complex128 intermediate."""
+    out = np.empty((rows, cols), dtype=np.complex64, order="F")
+    scale = np.float32(1.0 / math.sqrt(2.0))
+    for s in range(cols):
+        rng = np.random.default_rng([seed, s])
+        col = out[:, s]
+        col.real = rng.standard_normal(rows, dtype=np.float32) * scale
+        col.imag = rng.standard_normal(rows, dtype=np.float32) * scale
+    return out
+
+
 def gaussian_sketch(rows: int, cols: int, seed: int) -> np.ndarray:
     """Complex Gaussian test matrix for randomized range finding (column-major, complex128)."""
     return cn01((rows, cols), seed)

@@ -50,6 +50,12 @@ class zbc_compress_stats(C.Structure):
                 ("max_rel_err", C.c_double)]
 
 
+class zbc_rank_model(C.Structure):
+    _fields_ = [("mlp", C.c_void_p), ("features", C.c_void_p), ("oversample", C.c_int32),
+                ("fixed_width", C.c_int32), ("sketch1", C.c_void_p), ("sketch2", C.c_void_p),
+                ("sketch3", C.c_void_p), ("lmax", C.c_int32)]
+
+
 class zbc_cross_params(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("s0", C.c_int32), ("over", C.c_int32), ("rmax", C.c_int32)]
 
@@ -60,8 +66,8 @@ class zbc_cross_stats(C.Structure):
 
 class zbc_aca_stats(C.Structure):
     _fields_ = [("rank", C.c_int32), ("converged", C.c_int32), ("row_restarts", C.c_int32),
-                ("max_tucker_rank", C.c_int32), ("s2", C.c_double), ("last_term", C.c_double),
-                ("max_tucker_err", C.c_double)]
+                ("max_tucker_rank", C.c_int32), ("tucker_fallbacks", C.c_int32), ("reserved", C.c_int32),
+                ("s2", C.c_double), ("last_term", C.c_double), ("max_tucker_err", C.c_double)]
 
 
 _lib = None
@@ -81,20 +87,21 @@ def lib():
             "vsie_assemble_columns": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, vp, i64, i32, vp], i32),
             "vsie_assemble_columns_op": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, vp, i32, i32, i32, i32, vp, i64,
                                           i32, vp], i32),
-            "tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, i32, C.POINTER(vp),
-                                 C.POINTER(zbc_compress_stats), vp], i32),
+            "tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, i32, C.POINTER(zbc_rank_model),
+                                 i32, C.POINTER(vp), C.POINTER(zbc_compress_stats), vp], i32),
             "zbc_matvec": ([vp, vp, i64, i32, vp, i64, i32, vp], i32),
             "zbc_rmatvec": ([vp, vp, i64, i32, vp, i64, i32, vp], i32),
             "zbc_free": ([vp], i32),
             "zbc_get_info": ([vp, C.POINTER(zbc_info)], i32),
             "zbc_memory_bytes": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], i32),
+            "zbc_device_bytes": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], i32),
             "zbc_create_from_host": ([C.POINTER(zbc_grid), i32, i32, i32, vp, vp, i64, vp, C.POINTER(vp)], i32),
             "zbc_export_host": ([vp, vp, vp, vp], i32),
             "zbc_save": ([vp, C.c_char_p], i32),
             "zbc_load": ([C.c_char_p, C.POINTER(vp)], i32),
             "zbc_tc_selftest": ([vp, vp, vp, i32, i32, i32], i32),
-            "aca_compress": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, i32, dbl, i32, i32, dbl,
-                              C.POINTER(vp), C.POINTER(zbc_aca_stats), vp, vp], i32),
+            "aca_compress": ([C.POINTER(zbc_grid), C.POINTER(zbc_segments), dbl, i32, dbl, i32, i32, dbl, i32,
+                              C.POINTER(zbc_rank_model), C.POINTER(vp), C.POINTER(zbc_aca_stats), vp, vp], i32),
             "tucker_compress_randomized": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, vp, vp, vp, vp, i32,
                                             C.POINTER(vp), C.POINTER(zbc_compress_stats), vp], i32),
             "zbc_mlp_num_params": ([], i32),
@@ -108,6 +115,7 @@ def lib():
             "zbc_rank_widths": ([vp, vp, i32, C.POINTER(zbc_grid), i32, vp, vp], i32),
             "zbc_rmatvec_noalloc": ([vp, vp, i64, i32, vp, i64, vp], i32),
             "zbc_product_status": ([vp, vp], i32),
+            "zbc_test_wait_limit": ([vp, C.c_uint32], i32),
             "zbc_tune": ([vp, i32, vp, vp], i32),
             "cross_tucker_compress": ([vp, i64, i32, C.POINTER(zbc_grid), i32, i32, dbl, C.POINTER(zbc_cross_params),
                                        vp, i32, C.POINTER(vp), C.POINTER(zbc_compress_stats),
@@ -175,6 +183,11 @@ def from_colmajor(t) -> np.ndarray:
     return t.detach().cpu().numpy().T
 
 
+def from_colmajor_rows(t, rows) -> np.ndarray:
+    """Rows `rows` (an int64 CUDA tensor) of a column-major buffer, as a host (len(rows), cols) array."""
+    return t.index_select(1, rows).cpu().numpy().T
+
+
 def grid_struct(grid) -> zbc_grid:
     return zbc_grid(grid.n1, grid.n2, grid.n3, grid.h, getattr(grid, "mask_radius", 0.0))
 
@@ -202,6 +215,12 @@ class Handle:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib().zbc_memory_bytes(self.ptr, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
+
+    def device_bytes(self):
+        """{"pool", "caches", "work"}: device bytes this handle holds now (zbc_device_bytes)."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().zbc_device_bytes(self.ptr, C.byref(a), C.byref(b), C.byref(c)))
+        return {"pool": a.value, "caches": b.value, "work": c.value}
 
     def export(self):
         """(ranks (M, q, 3) int32, pool complex64, V (m x M) or None)."""
@@ -322,15 +341,28 @@ def vsie_assemble_columns_op(grid, dsegs: DeviceSegments, freq_hz: float, cols, 
     return out
 
 
-def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, append_to: Handle | None = None, stream=None):
-    """cols: column-major buffer (ncols, ld).  Returns (Handle, stats)."""
+def rank_model(sketches, lmax: int, mlp=None, features=None, oversample=4, fixed_width=0) -> zbc_rank_model:
+    """Inputs of the randomized methods of tucker_compress.  sketches: three complex64 CUDA tensors
+    holding Omega_g column-major (shape (lmax, N_g)); mlp / features (CUDA float32, ncols x 7) for
+    RANDOMIZED_LEARNED, fixed_width for RANDOMIZED_FIXED.  The structure refers to the tensors'
+    memory: keep them alive while it is used."""
+    return zbc_rank_model(mlp.ptr if mlp is not None else None,
+                          features.data_ptr() if features is not None else None, int(oversample),
+                          int(fixed_width), _ptr(sketches[0]), _ptr(sketches[1]), _ptr(sketches[2]), int(lmax))
+
+
+def tucker_compress(cols, grid, tol: float, q=3, method=HOSVD, model: zbc_rank_model | None = None,
+                    append_to: Handle | None = None, stream=None):
+    """cols: column-major buffer (ncols, ld).  method: HOSVD, RANDOMIZED_LEARNED or
+    RANDOMIZED_FIXED (the latter two need `model`, see rank_model).  Returns (Handle, stats)."""
     import torch
     g = grid_struct(grid)
     dt = C128 if cols.dtype == torch.complex128 else C64
     h = C.c_void_p(append_to.ptr.value if append_to is not None else None)
     st = zbc_compress_stats()
     _check(lib().tucker_compress(_ptr(cols), _ld(cols), cols.shape[0], C.byref(g), q, dt, tol, method,
-                                 C.byref(h), C.byref(st), _stream(stream)))
+                                 C.byref(model) if model is not None else None, C64, C.byref(h), C.byref(st),
+                                 _stream(stream)))
     if append_to is not None:
         return append_to, st
     return Handle(h), st
@@ -380,15 +412,17 @@ def cross_tucker_assemble(grid, dsegs: DeviceSegments, freq_hz: float, cols, tol
 
 
 def aca_compress(grid, dsegs: DeviceSegments, freq_hz: float, tol: float, max_rank: int, mode=ACA_DENSE_U,
-                 tucker_tol: float = 0.0, q=3, stream=None):
-    """Returns (Handle with U (Tucker) and V, stats, pivots array (r_c, 2))."""
+                 tucker_tol: float = 0.0, q=3, method=HOSVD, model: zbc_rank_model | None = None, stream=None):
+    """method: how U's tensors are compressed (HOSVD, or RANDOMIZED_FIXED with `model`, see
+    rank_model).  Returns (Handle with U (Tucker) and V, stats, pivots array (r_c, 2))."""
     g = grid_struct(grid)
     s = dsegs.struct()
     h = C.c_void_p()
     st = zbc_aca_stats()
     piv = np.zeros(2 * max_rank, dtype=np.int32)
-    _check(lib().aca_compress(C.byref(g), C.byref(s), freq_hz, q, tol, max_rank, mode, tucker_tol, C.byref(h),
-                              C.byref(st), piv.ctypes.data_as(C.c_void_p), _stream(stream)))
+    _check(lib().aca_compress(C.byref(g), C.byref(s), freq_hz, q, tol, max_rank, mode, tucker_tol, method,
+                              C.byref(model) if model is not None else None, C.byref(h), C.byref(st),
+                              piv.ctypes.data_as(C.c_void_p), _stream(stream)))
     return Handle(h), st, piv[:2 * st.rank].reshape(-1, 2)
 
 
@@ -494,9 +528,16 @@ def zbc_tune(h: Handle, p: int, stream=None) -> dict:
     return dict(zip(TUNE_VARIANTS, [float(x) for x in t]))
 
 
+def zbc_test_wait_limit(h: Handle, polls: int):
+    """Test hook: the next FP32 SIMT adjoint launch on h allows its consumers' first stage wait
+    `polls` polls (0: give up at once, so zbc_product_status reports ZBC_ETIMEOUT)."""
+    _check(lib().zbc_test_wait_limit(h.ptr, int(polls)))
+
+
 def zbc_product_status(h: Handle, stream=None):
-    """Synchronise the stream and raise ZbcError(ZBC_ETIMEOUT) if a product kernel of h gave up
-    a bounded device wait since the last check."""
+    """Synchronise the stream; raise ZbcError(ZBC_ETIMEOUT) if a product kernel of h gave up a
+    bounded device wait since the last check, else ZbcError(ZBC_ENAN) if one read a NaN or Inf
+    from X or Phi.  Clears the handle's error word."""
     _check(lib().zbc_product_status(h.ptr, _stream(stream)))
 
 

@@ -37,7 +37,7 @@ def test_without_a_device_calls_fail_with_a_status(zbc):
     cols = np.array([0, 1], np.int32)
     calls = {
         "tucker_compress": lambda: L.tucker_compress(fake, 3 * nv, 2, C.byref(g), 3, zbc.C64, 1e-5, zbc.HOSVD,
-                                                     C.byref(h), C.byref(st), None),
+                                                     None, zbc.C64, C.byref(h), C.byref(st), None),
         "cross_tucker_assemble": lambda: L.cross_tucker_assemble(C.byref(g), C.byref(segs), 298.2e6,
                                                                  cols.ctypes.data_as(C.c_void_p), 2, 3, 0, 1, 1e-5,
                                                                  None, None, 0, C.byref(h), C.byref(st), C.byref(xs),
