@@ -228,7 +228,8 @@ def workload(name: str) -> Workload:
     tiny      : 24^3 grid, 5 mm, 64 segments on a circle of radius 0.15 m, tol 1e-8, p = 1
     precision : 96^3 grid, 2 mm, 8 loops x 128 segments on a cylinder (r 0.14, L 0.20), tol 1e-6, p = 16
     batching  : 160x160x128, 1.5 mm, 16 loops x 256 segments (r 0.16, L 0.25), ACA tol 1e-6, p <= 128
-                voxels beyond radius 0.16 - 2h are masked (the coil crosses the grid corners)
+                voxels beyond radius 0.14 m (2 cm inside the coil) are masked (the coil crosses the
+                grid corners)
     learned   : 128^3, 2 mm, 4096 random segments on cylinders r 0.12..0.20, tol 1e-6
     large     : 320x320x256, 1 mm, 32 loops x 64 segments (r 0.30, L 0.40), ACA tol 1e-5, p = 32
     """
@@ -240,7 +241,7 @@ def workload(name: str) -> Workload:
         return Workload(name, g, cylinder_array(0.14, 0.20, 8, 1024), FREQ_HZ, 1e-6, 16)
     if name == "batching":
         h = 0.0015
-        g = Grid(160, 160, 128, h, mask_radius=0.16 - 2 * h)
+        g = Grid(160, 160, 128, h, mask_radius=0.16 - 0.02)
         return Workload(name, g, cylinder_array(0.16, 0.25, 16, 4096), FREQ_HZ, 1e-6, 128, aca=True)
     if name == "learned":
         g = Grid(128, 128, 128, 0.002)

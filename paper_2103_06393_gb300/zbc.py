@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libzbc.so")
 
 ZBC_OK, ZBC_EINVAL, ZBC_ENOMEM, ZBC_ECUDA, ZBC_ETOL, ZBC_ETIMEOUT, ZBC_ENAN, ZBC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
-FP32_SIMT, TF32X3, BF16X3, AUTO, TC2, TC_MODE1 = 0, 1, 2, 3, 4, 5
+FP32_SIMT, TF32X3, BF16X3, AUTO, TC2, TC_MODE1, TC_DC = 0, 1, 2, 3, 4, 5, 6
 HOSVD, RANDOMIZED_LEARNED, RANDOMIZED_FIXED = 0, 1, 2
 ACA_DENSE_U, ACA_ALG3 = 0, 1
 PRECISIONS = {"fp32_simt": FP32_SIMT, "tf32x3": TF32X3, "bf16x3": BF16X3}
@@ -515,7 +515,7 @@ def zbc_rmatvec_noalloc(h: Handle, Phi, Psi, stream=None):
 
 
 TUNE_VARIANTS = (
-    "fwd_simt6", "fwd_simt9", "fwd_tf32x3", "fwd_bf16x3", "fwd_tc2", "fwd_mode1",
+    "fwd_simt6", "fwd_simt9", "fwd_tf32x3", "fwd_bf16x3", "fwd_tc2", "fwd_mode1", "fwd_dc",
     "adj_simt6", "adj_simt9", "adj_mode1",
 )
 
