@@ -68,6 +68,11 @@ typedef enum { ZBC_C64 = 0, ZBC_C128 = 1 } zbc_dtype;
  *             Forward: per block of 128 (i2 i3, RHS) rows and i1 tile of at most 96,
  *             Y^k = U1 (W X) over all (column, rank) rows, W X generated on CUDA cores, the
  *             tensor-core sum folded into FP32 every 192 rows.
+ * TC_DC     : (forward only) decompression then contraction per voxel block: Z for 32 i1 x 4T i23
+ *             voxels and a chunk of 8 stored columns from U1 and the cached W on CUDA cores
+ *             (FP32, written as fp16 hi + lo), the contraction with X as a tcgen05 GEMM
+ *             (M = 128 voxels, N = 2 x 16 .. 2 x 128 right-hand sides, 3 products, FP32
+ *             accumulation folded into an FP32 sum in tensor memory every 64 columns).
  * AUTO      : the form (and CTA shape) zbc_tune measured fastest for this handle and this
  *             right-hand-side class; before any tuning, BF16X3 for the forward product when
  *             p >= 8 and FP32_SIMT otherwise.  Every form meets the same 1e-5 relative accuracy,
@@ -78,7 +83,8 @@ typedef enum {
   ZBC_BF16X3 = 2,
   ZBC_AUTO = 3,
   ZBC_TC2 = 4,
-  ZBC_TC_MODE1 = 5
+  ZBC_TC_MODE1 = 5,
+  ZBC_TC_DC = 6
 } zbc_precision;
 
 typedef enum { ZBC_HOSVD = 0, ZBC_RANDOMIZED_LEARNED = 1, ZBC_RANDOMIZED_FIXED = 2 } zbc_tucker_method;
@@ -424,11 +430,11 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
 /*
  * zbc_tune -- autotuner of the product kernels (no counterpart in the paper).  Times, on this
  * handle with p right-hand sides (zero-filled scratch operands), every variant of
- *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2, TC_MODE1
+ *   zbc_matvec : FP32_SIMT with 6 and with 9 compute warps per CTA, TF32X3, BF16X3, TC2, TC_MODE1, TC_DC
  *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA, TC_MODE1
  * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
  * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the faster SIMT shape).
- *   times_ms_host : optional float[9], the variants' times in the order above (ms per call;
+ *   times_ms_host : optional float[10], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
  */

@@ -107,6 +107,10 @@ struct HalfDesc {
 struct Mode1Cache;  // operands of the mode-1 adjoint (products_mode1.cu), built on its first use
 void mode1_release(Mode1Cache* c);
 
+struct DcCache;
+void dc_release(DcCache* c);
+int64_t dc_bytes(const DcCache* c);
+
 struct DecompCache {
   float2* data = nullptr;   // W blocks and tile-blocked U1
   CacheDesc* d_desc = nullptr;
@@ -116,6 +120,7 @@ struct DecompCache {
   HalfDesc* d_half = nullptr;
   int kb1_max = 0;
   Mode1Cache* mode1 = nullptr;
+  DcCache* dc = nullptr;    // operands of the decompress-and-contract tensor-core forward (products_dc.cu)
   int64_t bytes = 0;        // device bytes held (W, U1, descriptors, fp16 copies; not mode1's)
 };
 int build_decomp_cache(Handle& h, cudaStream_t st);

@@ -21,6 +21,7 @@ void cache_release(DecompCache* c) {
   if (c->half) cudaFree(c->half);
   if (c->d_half) cudaFree(c->d_half);
   mode1_release(c->mode1);
+  dc_release(c->dc);
   delete c;
 }
 

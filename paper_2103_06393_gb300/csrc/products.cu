@@ -9,6 +9,7 @@ int matvec_tc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t
               cudaStream_t st);
 int matvec_tc2(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
 int matvec_mode1(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
+int matvec_dc(Handle& h, const float2* X, int64_t ldx, int p, float2* Y, int64_t ldy, cudaStream_t st);
 int aca_pre(const Handle& h, const float2* X, int64_t ldx, int p, float2* Xp, cudaStream_t st);
 int aca_post(const Handle& h, const float2* Psip, int p, float2* Psi, int64_t ldpsi, cudaStream_t st);
 
@@ -26,6 +27,7 @@ static int matvec_impl(Handle& h, const float2* X, int64_t ldx, int p, float2* Y
   if (prec == ZBC_FP32_SIMT) return matvec_simt(h, Xe, ldxe, p, Y, ldy, warps, st);
   if (prec == ZBC_TC2) return matvec_tc2(h, Xe, ldxe, p, Y, ldy, st);
   if (prec == ZBC_TC_MODE1) return matvec_mode1(h, Xe, ldxe, p, Y, ldy, st);
+  if (prec == ZBC_TC_DC) return matvec_dc(h, Xe, ldxe, p, Y, ldy, st);
   return matvec_tc(h, Xe, ldxe, p, Y, ldy, prec, st);
 }
 
@@ -59,7 +61,7 @@ extern "C" int zbc_matvec(const zbc_handle* hh, const void* X, int64_t ldx, int 
   ZBC_CHECK_ARG(ldx >= h.m, "ldx (%lld) < m (%d)", (long long)ldx, h.m);
   ZBC_CHECK_ARG(ldy >= (int64_t)h.q * h.nv(), "ldy < q*n_v");
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
-                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1,
+                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1 || prec == ZBC_TC_DC,
                 "unknown precision %d", (int)prec);
   const int cls = rhs_class(p);
   int warps = h.tune_fwd_warps[cls];
@@ -77,7 +79,7 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   ZBC_CHECK_ARG(ldphi >= (int64_t)h.q * h.nv(), "ldphi < q*n_v");
   ZBC_CHECK_ARG(ldpsi >= h.m, "ldpsi (%lld) < m (%d)", (long long)ldpsi, h.m);
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_TF32X3 || prec == ZBC_BF16X3 || prec == ZBC_AUTO ||
-                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1,
+                    prec == ZBC_TC2 || prec == ZBC_TC_MODE1 || prec == ZBC_TC_DC,
                 "unknown precision %d", (int)prec);
   ZBC_CHECK_ARG(prec == ZBC_FP32_SIMT || prec == ZBC_AUTO || prec == ZBC_TC_MODE1,
                 "the adjoint product's forms are ZBC_FP32_SIMT, ZBC_TC_MODE1 and ZBC_AUTO");
@@ -109,10 +111,11 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
     zbc_precision prec;
     int warps;
   };
-  constexpr int NV = 9, NF = 6;  // the first NF variants are forward forms
-  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6},  {true, ZBC_FP32_SIMT, 9}, {true, ZBC_TF32X3, 0},
-                            {true, ZBC_BF16X3, 0},     {true, ZBC_TC2, 0},       {true, ZBC_TC_MODE1, 0},
-                            {false, ZBC_FP32_SIMT, 6}, {false, ZBC_FP32_SIMT, 9}, {false, ZBC_TC_MODE1, 0}};
+  constexpr int NV = 10, NF = 7;  // the first NF variants are forward forms
+  const Variant vars[NV] = {{true, ZBC_FP32_SIMT, 6},  {true, ZBC_FP32_SIMT, 9},  {true, ZBC_TF32X3, 0},
+                            {true, ZBC_BF16X3, 0},     {true, ZBC_TC2, 0},        {true, ZBC_TC_MODE1, 0},
+                            {true, ZBC_TC_DC, 0},      {false, ZBC_FP32_SIMT, 6}, {false, ZBC_FP32_SIMT, 9},
+                            {false, ZBC_TC_MODE1, 0}};
   float t[NV];
   int status = ZBC_OK;
   for (int i = 0; i < NV && status == ZBC_OK; ++i) {

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128) mode1_build_kernel(const float2* __restri
 
 int64_t cache_bytes(const DecompCache* c) {
   if (!c) return 0;
-  return c->bytes + (c->mode1 ? c->mode1->bytes : 0);
+  return c->bytes + (c->mode1 ? c->mode1->bytes : 0) + dc_bytes(c->dc);
 }
 
 int build_mode1_cache(Handle& h, cudaStream_t st) {

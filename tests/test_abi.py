@@ -49,7 +49,7 @@ def test_binding_enums_match_the_header():
     from paper_2103_06393_gb300 import zbc
     text = open(os.path.join(ROOT, "include", "zbc.h")).read()
     values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ZBC_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
-    for name in ("FP32_SIMT", "TF32X3", "BF16X3", "AUTO", "TC2", "TC_MODE1"):
+    for name in ("FP32_SIMT", "TF32X3", "BF16X3", "AUTO", "TC2", "TC_MODE1", "TC_DC"):
         assert getattr(zbc, name) == values["ZBC_" + name], name
     for name in ("ZBC_OK", "ZBC_EINVAL"):
         assert getattr(zbc, name) == values[name], name

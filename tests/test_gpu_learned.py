@@ -228,3 +228,45 @@ def test_tucker_compress_rejects_bad_model_and_storage():
         with pytest.raises(zbc.ZbcError) as e:
             zbc.tucker_compress(Zd, g, 1e-6, method=method, model=model)
         assert e.value.status == zbc.ZBC_EINVAL
+
+
+def test_trained_network_beats_fixed_widths():
+    """What the learned part gains (spec ablation): the MLP trained on the GPU on HOSVD ranks
+    of 96 columns, then 64 other columns compressed with its widths and with one fixed width equal
+    to the learned widths' mean (the same sketch budget spread evenly).  The trained widths must
+    fall back to the HOSVD less often, and the learned and the fixed-max width (largest training
+    rank + 4, the method without the network) must meet the tolerance."""
+    w = inputs.scaled_workload("learned", (40, 36, 32), m=160)
+    g, s = w.grid, w.segments
+    ds = zbc.DeviceSegments(s)
+    tol, lmax = 1e-6, 32
+    feats = inputs.rank_features(g, s)
+    train, test = np.arange(96), np.arange(96, 160)
+
+    def assemble(cols):
+        Z = zbc.colmajor(3 * g.nv, len(cols), torch.complex64)
+        zbc.vsie_assemble_columns(g, ds, w.freq_hz, torch.from_numpy(cols.astype(np.int32)).cuda(), Z)
+        return Z
+
+    h, _ = zbc.tucker_compress(assemble(train), g, tol)
+    rt = h.export()[0].reshape(-1, 9)
+    M = zbc.Mlp(pack(mlp.init_params(0)))
+    hist = M.train(torch.from_numpy(feats[train]).cuda(), torch.from_numpy(np.log(rt.astype(np.float32))).cuda(),
+                   1500, 3e-3).cpu().numpy()
+    assert hist[-1] < 0.3 * hist[0]
+    ft = torch.from_numpy(feats[test]).cuda()
+    widths = M.widths(ft, g, oversample=4)
+    sk = [zbc.to_colmajor(o) for o in inputs.mode_sketches(g, lmax, seed=19)]
+    Z = assemble(test)
+    _, st_l = zbc.tucker_compress(Z, g, tol, method=zbc.RANDOMIZED_LEARNED,
+                                  model=zbc.rank_model(sk, lmax, mlp=M, features=ft, oversample=4))
+    mean_w = int(round(float(_effective_widths(widths, g.shape, lmax).mean())))
+    _, st_m = zbc.tucker_compress(Z, g, tol, method=zbc.RANDOMIZED_FIXED,
+                                  model=zbc.rank_model(sk, lmax, fixed_width=mean_w))
+    _, st_x = zbc.tucker_compress(Z, g, tol, method=zbc.RANDOMIZED_FIXED,
+                                  model=zbc.rank_model(sk, lmax, fixed_width=int(rt.max()) + 4))
+    print(f"fallbacks: learned {st_l.n_fallback}, fixed at the learned mean {mean_w}: {st_m.n_fallback}, "
+          f"fixed at the training maximum {int(rt.max()) + 4}: {st_x.n_fallback} of {st_l.n_tensors}")
+    assert st_l.n_fallback < st_m.n_fallback
+    for st in (st_l, st_m, st_x):
+        assert st.max_rel_err <= tol * (1 + 1e-9)
