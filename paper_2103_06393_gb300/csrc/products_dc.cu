@@ -8,7 +8,7 @@
 //                     of the decompression; W = G x2 U2 x3 U3 from the handle's decompression cache)
 //                     in FP32 on the CUDA cores, one i1 per thread for T values of i23, so each U1
 //                     value a thread loads serves T voxels; written as fp16 hi / lo pieces of the
-//                     MMA's A operand (T tiles of 128 voxels x [Re Z | Im Z] of the chunk's 8
+//                     MMA's A operand (T tiles of 128 voxels x (Re Z, Im Z) of the chunk's 8
 //                     columns) in shared memory;
 //   MMA warp        : per tile D[voxel][(Re | Im) Y of P right-hand sides] += A B^T, B = the chunk's
 //                     rows of X' as [[Re X, Im X], [-Im X, Re X]] (fp16 hi / lo, built per call):
@@ -289,9 +289,12 @@ __host__ __device__ __forceinline__ uint32_t dc_off(uint32_t n, uint32_t kk) {
   return (n >> 3) * 256u + (kk >> 3) * 128u + (n & 7u) * 16u + (kk & 7u) * 2u;
 }
 
-// B blocks: [pass sc][chunk c][term hi | lo][2P rows][16]: row n < P (Re Y of s = n):
-// [Re X'[j, s], -Im X'[j, s]]; row n >= P (Im Y of s = n - P): [Im X', Re X'], over the chunk's
-// columns j0 + (kk % 8) (zero beyond the chunk), X' scaled by 2^(kDcShift - ex_s).
+// K slots of a chunk: kk = 8 h + 4 part + c (h, part in {0, 1}, c < 4) holds column j0 + 4 h + c,
+// its real part (part 0) or imaginary part (part 1), so that a generator thread writes the 8 slots
+// of its four columns as one 16-byte store.
+// B blocks: [pass sc][chunk c][term hi | lo][2P rows][16]: row n < P (Re Y of s = n): Re X'[j, s]
+// in the real slots, -Im X'[j, s] in the imaginary slots; row n >= P (Im Y of s = n - P): Im X'
+// and Re X' (zero beyond the chunk), X' scaled by 2^(kDcShift - ex_s).
 // One thread per (sc, c, n, kk).
 __global__ void __launch_bounds__(256) dc_b_kernel(const float2* __restrict__ X, int64_t ldx, int p, int P, int NC,
                                                    int nsc, const int4* __restrict__ chunks,
@@ -304,11 +307,11 @@ __global__ void __launch_bounds__(256) dc_b_kernel(const float2* __restrict__ X,
   const int64_t blk = e / per;  // sc * NC + c
   const int c = (int)(blk % NC), sc = (int)(blk / NC);
   const int4 ch = chunks[c];
-  const int jl = kk % 8, s = sc * P + (n % P);
+  const int jl = (kk >> 3) * 4 + (kk & 3), s = sc * P + (n % P);
   float v = 0.f;
   if (jl < ch.y && s < p) {
     const float2 x = X[ch.x + jl + ldx * s];
-    const bool re_row = n < P, first = kk < 8;
+    const bool re_row = n < P, first = ((kk >> 2) & 1) == 0;
     v = re_row ? (first ? x.x : -x.y) : (first ? x.y : x.x);
     v = ldexpf(v, kDcShift - ex[s]);  // on the value: 2^(kDcShift - ex) alone may not be a float
   }
@@ -507,7 +510,12 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
     // ---------------- 8 warps: generate A, fold D into S, write Y ----------------
     const int hg = warp >> 2;                      // warpgroup: columns [4 hg, 4 hg + 4) of a chunk
     const int w4 = warp & 3;                       // TMEM lanes [32 w4, 32 w4 + 32)
-    const int row = w4 * 32 + lane;                // A / D row within a tile
+    // Row 32 b + i1 of a tile is the voxel (32 g1 + i1, i23_0 + 4 t + b).  The folds and the
+    // epilogue read lane row = 32 w4 + lane; the generator's thread takes i1 = 8 w4 + (lane & 7) and
+    // b = lane >> 3, so that a warp's U1 loads touch 8 rows (one wavefront) and the four warps of a
+    // warpgroup load disjoint U1 rows.
+    const int gi1 = 8 * w4 + (lane & 7), gb = lane >> 3;
+    const int row = 32 * gb + gi1;                 // the generator's A row within a tile
     const uint32_t lanebase = (uint32_t)(w4 * 32) << 16;
     uint32_t gc = 0, gs = 0;
     bool bad = false;
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
         const unsigned char* sb = smem + (size_t)st * prm.stage_bytes;
         const DcHdr* hd = reinterpret_cast<const DcHdr*>(sb + prm.h_off);
         const int nc = hd->nc;
-        const float4* __restrict__ Us = reinterpret_cast<const float4*>(sb) + lane;
+        const float4* __restrict__ Us = reinterpret_cast<const float4*>(sb) + gi1;
         const float4* __restrict__ Ws = reinterpret_cast<const float4*>(sb + prm.w_off);
         float zr[T][4], zi[T][4];
 #pragma unroll
@@ -578,7 +586,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
           if (cc < nc) {
             const int n2 = hd->r1p[cc] / 2;
             const float4* U = Us + hd->uo[cc];                       // pair a2 at U[32 a2]
-            const float4* W = Ws + hd->wo[cc] + w4 * n2;             // tile t at W[4 n2 t + a2]
+            const float4* W = Ws + hd->wo[cc] + gb * n2;             // tile t at W[4 n2 t + a2]
             float4 u = U[0];
             float4 wv[T];
 #pragma unroll
@@ -610,7 +618,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
             zi[t][c4] = (ae[t].y + ao[t].y) * fz;
           }
         }
-        // A pieces: Re Z of columns 4 hg .. 4 hg + 3 at K = 4 hg .., Im Z at K = 8 + 4 hg .., hi and lo
+        // A pieces: Re Z of columns 4 hg .. 4 hg + 3 at K = 8 hg .. 8 hg + 3, Im Z at K = 8 hg + 4 ..,
+        // one 16-byte store per term (the 32 rows of a warp then fill every bank once per wavefront)
         unsigned char* ab0 = abuf + ab * kABuf;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -629,10 +638,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
           }
           unsigned char* th = ab0 + (2 * t) * kTile;
           unsigned char* tl = ab0 + (2 * t + 1) * kTile;
-          *reinterpret_cast<uint2*>(th + dc_off(row, 4 * hg)) = make_uint2(hr[0], hr[1]);
-          *reinterpret_cast<uint2*>(th + dc_off(row, 8 + 4 * hg)) = make_uint2(hi_[0], hi_[1]);
-          *reinterpret_cast<uint2*>(tl + dc_off(row, 4 * hg)) = make_uint2(lr[0], lr[1]);
-          *reinterpret_cast<uint2*>(tl + dc_off(row, 8 + 4 * hg)) = make_uint2(li[0], li[1]);
+          *reinterpret_cast<uint4*>(th + dc_off(row, 8 * hg)) = make_uint4(hr[0], hr[1], hi_[0], hi_[1]);
+          *reinterpret_cast<uint4*>(tl + dc_off(row, 8 * hg)) = make_uint4(lr[0], lr[1], li[0], li[1]);
         }
         tc::fence_proxy_async();  // the generic-proxy stores above are read by the tensor cores
         __syncwarp();
