@@ -95,6 +95,9 @@ typedef struct {
   int32_t n1, n2, n3;   /* voxels per axis */
   double h;             /* voxel edge (m) */
   double mask_radius;   /* voxels with sqrt(x^2+y^2) > mask_radius are zero rows; <= 0: no mask */
+  double mask_box;      /* voxels with max(|x|, |y|) > mask_box are zero rows; <= 0: no mask.  A box
+                           mask is a product of per-axis indicators, so it leaves the Tucker ranks
+                           of a column's tensors as they are on the kept box */
 } zbc_grid;
 
 typedef struct {
@@ -434,6 +437,8 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
  *   zbc_rmatvec: FP32_SIMT with 6 and with 9 compute warps per CTA, TC_MODE1
  * and records the fastest of each for p's right-hand-side class (p = 1, 2, 3-4, 5-8, 9-16,
  * 17-32, 33-64, 65+), which ZBC_AUTO then uses (zbc_rmatvec_noalloc uses the faster SIMT shape).
+ * Each variant runs once untimed, then is timed over two calls, or over one when that call took
+ * more than 1.5 times the best of its direction so far (the tensor-core forms are timed first).
  *   times_ms_host : optional float[10], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.

@@ -145,7 +145,7 @@ def dense_source(A: np.ndarray):
 
 
 def green_source(n, h, centre, tangent, length, freq_hz, e: int, k: int, q: int = 3, mask_radius=0.0,
-                 operator="N", nq=1):
+                 operator="N", nq=1, mask_box=0.0):
     """entry() of component k of column e of the coupling matrix (Eq. nNt / Eq. nKt), evaluated
     voxel by voxel from the Green's function (the column is never assembled)."""
     n1, n2, _ = n
@@ -155,21 +155,22 @@ def green_source(n, h, centre, tangent, length, freq_hz, e: int, k: int, q: int 
         shape = i1.shape
         v = (i1 + n1 * (i2 + n2 * i3)).reshape(-1)
         z = greens.assemble_columns(n, h, centre, tangent, length, freq_hz, [e], q=q, mask_radius=mask_radius,
-                                    rows=v, operator=operator, nq=nq)[:, 0]
+                                    rows=v, operator=operator, nq=nq, mask_box=mask_box)[:, 0]
         return z[k * v.size:(k + 1) * v.size].reshape(shape)
 
     return entry
 
 
 def compress_columns(n, h, centre, tangent, length, freq_hz, cols, tol: float, q: int = 3, mask_radius=0.0,
-                     operator="N", nq=1, checks=(), **kw):
+                     operator="N", nq=1, checks=(), mask_box=0.0, **kw):
     """Every column e of cols -> q Tucker tensors from fibres of the Green's function; a list over
     columns of a list over components of (G, [U1, U2, U3], info), info['check_err'] on `checks`."""
     out = []
     for e in np.atleast_1d(cols):
         comps = []
         for k in range(q):
-            src = green_source(n, h, centre, tangent, length, freq_hz, int(e), k, q, mask_radius, operator, nq)
+            src = green_source(n, h, centre, tangent, length, freq_hz, int(e), k, q, mask_radius, operator, nq,
+                               mask_box)
             G, Us, info = cross_tucker(src, n, tol, **kw)
             info["check_err"] = check_error(src, G, Us, n, checks) if len(checks) else None
             comps.append((G, Us, info))

@@ -109,16 +109,20 @@ def voxel_centres(n1: int, n2: int, n3: int, h: float) -> np.ndarray:
     return np.stack([x, y, z], axis=1)
 
 
-def voxel_mask(n1, n2, n3, h, mask_radius) -> np.ndarray:
-    """True for voxels kept; voxels with sqrt(x^2+y^2) > mask_radius are dropped (0 = keep all)."""
+def voxel_mask(n1, n2, n3, h, mask_radius, mask_box=0.0) -> np.ndarray:
+    """True for voxels kept; voxels with sqrt(x^2+y^2) > mask_radius (if > 0) or with
+    max(|x|, |y|) > mask_box (if > 0) are dropped."""
     r = voxel_centres(n1, n2, n3, h)
-    if mask_radius <= 0:
-        return np.ones(r.shape[0], dtype=bool)
-    return np.sqrt(r[:, 0] ** 2 + r[:, 1] ** 2) <= mask_radius
+    keep = np.ones(r.shape[0], dtype=bool)
+    if mask_box > 0:
+        keep &= (np.abs(r[:, 0]) <= mask_box) & (np.abs(r[:, 1]) <= mask_box)
+    if mask_radius > 0:
+        keep &= np.sqrt(r[:, 0] ** 2 + r[:, 1] ** 2) <= mask_radius
+    return keep
 
 
 def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_radius=0.0,
-                     rows=None, operator="N", nq=1) -> np.ndarray:
+                     rows=None, operator="N", nq=1, mask_box=0.0) -> np.ndarray:
     """Dense columns Z[:, cols] of the (q*n_v) x m coupling matrix, complex128, column-major.
 
     rows: optional subset of voxel indices v; the result then has q*len(rows) rows
@@ -132,7 +136,7 @@ def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_rad
     n1, n2, n3 = n
     k0 = wavenumber(freq_hz)
     rv = voxel_centres(n1, n2, n3, h)
-    keep = voxel_mask(n1, n2, n3, h, mask_radius)
+    keep = voxel_mask(n1, n2, n3, h, mask_radius, mask_box)
     if rows is not None:
         rows = np.asarray(rows)
         rv = rv[rows]
@@ -154,13 +158,13 @@ def assemble_columns(n, h, centre, tangent, length, freq_hz, cols, q=3, mask_rad
     return out
 
 
-def assemble_row(n, h, centre, tangent, length, freq_hz, row, q=3, mask_radius=0.0) -> np.ndarray:
+def assemble_row(n, h, centre, tangent, length, freq_hz, row, q=3, mask_radius=0.0, mask_box=0.0) -> np.ndarray:
     """One row Z[row, :] (all m columns), row = k*n_v + v."""
     n1, n2, n3 = n
     nv = n1 * n2 * n3
     k, v = divmod(int(row), nv)
     rv = voxel_centres(n1, n2, n3, h)[v]
-    if not voxel_mask(n1, n2, n3, h, mask_radius)[v]:
+    if not voxel_mask(n1, n2, n3, h, mask_radius, mask_box)[v]:
         return np.zeros(length.shape[0], dtype=np.complex128)
     G = dyadic_green(rv[None, :], centre, wavenumber(freq_hz))   # (m, 3, 3)
     f = np.einsum("eab,eb->ea", G, tangent) * (h ** 3 * length)[:, None]

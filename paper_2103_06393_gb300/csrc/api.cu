@@ -348,7 +348,7 @@ extern "C" int zbc_load(const char* path, zbc_handle** out) {
     set_error("%s is truncated", path);
     return ZBC_EIO;
   }
-  zbc_grid g{fh.n1, fh.n2, fh.n3, 1.0, 0.0};
+  zbc_grid g{fh.n1, fh.n2, fh.n3, 1.0, 0.0, 0.0};
   return zbc_create_from_host(&g, fh.q, fh.M, fh.m, ranks.data(), pool.data(), fh.pool_elems,
                               fh.has_v ? v.data() : nullptr, out);
 }

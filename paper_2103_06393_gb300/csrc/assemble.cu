@@ -38,6 +38,7 @@ GreenGeom make_green(const zbc_grid* g, const zbc_segments* s, double freq_hz) {
   G.n3 = g->n3;
   G.h = g->h;
   G.mask_r = g->mask_radius;
+  G.mask_b = g->mask_box;
   G.k0 = wavenumber(freq_hz);
   G.centre = s->centre;
   G.tangent = s->tangent;

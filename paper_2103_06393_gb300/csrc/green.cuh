@@ -20,7 +20,7 @@ constexpr int kMaxQuad = 16;  // Gauss-Legendre points per segment, at most
 
 struct GreenGeom {
   int n1, n2, n3;
-  double h, mask_r, k0;
+  double h, mask_r, mask_b, k0;
   const double* centre;
   const double* tangent;
   const double* length;
@@ -39,6 +39,7 @@ __device__ __forceinline__ bool voxel_centre(const GreenGeom& G, int64_t v, doub
   x = __dmul_rn((double)i1 - (G.n1 - 1) / 2.0, G.h);
   y = __dmul_rn((double)i2 - (G.n2 - 1) / 2.0, G.h);
   z = __dmul_rn((double)i3 - (G.n3 - 1) / 2.0, G.h);
+  if (G.mask_b > 0.0 && (fabs(x) > G.mask_b || fabs(y) > G.mask_b)) return false;
   if (G.mask_r > 0.0) return !(sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))) > G.mask_r);
   return true;
 }

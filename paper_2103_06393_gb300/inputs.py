@@ -30,6 +30,7 @@ class Grid:
     n3: int
     h: float
     mask_radius: float = 0.0  # voxels with sqrt(x^2+y^2) > mask_radius are zero rows (0 = no mask)
+    mask_box: float = 0.0     # voxels with max(|x|, |y|) > mask_box are zero rows (0 = no mask)
 
     @property
     def nv(self) -> int:
@@ -227,9 +228,10 @@ def workload(name: str) -> Workload:
 
     tiny      : 24^3 grid, 5 mm, 64 segments on a circle of radius 0.15 m, tol 1e-8, p = 1
     precision : 96^3 grid, 2 mm, 8 loops x 128 segments on a cylinder (r 0.14, L 0.20), tol 1e-6, p = 16
-    batching  : 160x160x128, 1.5 mm, 16 loops x 256 segments (r 0.16, L 0.25), ACA tol 1e-6, p <= 128
-                voxels beyond radius 0.14 m (2 cm inside the coil) are masked (the coil crosses the
-                grid corners)
+    batching  : 160x160x128, 1.5 mm, 16 loops x 256 segments (r 0.16, L 0.25), tol 1e-6, p <= 128;
+                the coil crosses the grid's corners, so voxels outside the square |x|, |y| <=
+                (0.16 - 0.02) / sqrt(2) m (whose corners are 2 cm inside the coil) are masked: a box
+                mask, which keeps the Tucker ranks of the kept field (a circular mask would not)
     learned   : 128^3, 2 mm, 4096 random segments on cylinders r 0.12..0.20, tol 1e-6
     large     : 320x320x256, 1 mm, 32 loops x 64 segments (r 0.30, L 0.40), ACA tol 1e-5, p = 32
     """
@@ -241,7 +243,7 @@ def workload(name: str) -> Workload:
         return Workload(name, g, cylinder_array(0.14, 0.20, 8, 1024), FREQ_HZ, 1e-6, 16)
     if name == "batching":
         h = 0.0015
-        g = Grid(160, 160, 128, h, mask_radius=0.16 - 0.02)
+        g = Grid(160, 160, 128, h, mask_box=(0.16 - 0.02) / math.sqrt(2.0))
         return Workload(name, g, cylinder_array(0.16, 0.25, 16, 4096), FREQ_HZ, 1e-6, 128, aca=True)
     if name == "learned":
         g = Grid(128, 128, 128, 0.002)
@@ -257,7 +259,7 @@ def scaled_workload(name: str, n: tuple, m: int | None = None) -> Workload:
     (used for parity cases the oracle finishes in seconds).  m keeps the first m
     segments spread evenly over the coil."""
     w = workload(name)
-    g = Grid(n[0], n[1], n[2], w.grid.h, w.grid.mask_radius)
+    g = Grid(n[0], n[1], n[2], w.grid.h, w.grid.mask_radius, w.grid.mask_box)
     s = w.segments
     if m is not None and m < s.m:
         idx = np.linspace(0, s.m - 1, m).round().astype(int)

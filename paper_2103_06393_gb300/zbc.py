@@ -32,7 +32,7 @@ class ZbcError(RuntimeError):
 
 class zbc_grid(C.Structure):
     _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("n3", C.c_int32), ("h", C.c_double),
-                ("mask_radius", C.c_double)]
+                ("mask_radius", C.c_double), ("mask_box", C.c_double)]
 
 
 class zbc_segments(C.Structure):
@@ -189,7 +189,8 @@ def from_colmajor_rows(t, rows) -> np.ndarray:
 
 
 def grid_struct(grid) -> zbc_grid:
-    return zbc_grid(grid.n1, grid.n2, grid.n3, grid.h, getattr(grid, "mask_radius", 0.0))
+    return zbc_grid(grid.n1, grid.n2, grid.n3, grid.h, getattr(grid, "mask_radius", 0.0),
+                    getattr(grid, "mask_box", 0.0))
 
 
 class Handle:

@@ -26,7 +26,7 @@ def _case(mask_radius=None, n=(12, 12, 10), m=64):
         g = inputs.Grid(g.n1, g.n2, g.n3, g.h, mask_radius)
     s = w.segments
     Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m),
-                                mask_radius=g.mask_radius)
+                                mask_radius=g.mask_radius, mask_box=g.mask_box)
     return w, g, s, Z
 
 

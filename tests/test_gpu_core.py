@@ -31,7 +31,7 @@ def dense(w, cols=None):
     g, s = w.grid, w.segments
     cols = np.arange(s.m) if cols is None else cols
     return greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, cols,
-                                   mask_radius=g.mask_radius)
+                                   mask_radius=g.mask_radius, mask_box=g.mask_box)
 
 
 def gpu_assemble(w, dtype=torch.complex128, cols=None):
@@ -72,6 +72,17 @@ def test_assembly_complex64_and_mask_exact():
     assert (Zo == 0).any()
     Z32 = zbc.from_colmajor(gpu_assemble(w, torch.complex64))
     assert rel_cols(Z32, Zo).max() < 1e-7
+
+
+def test_assembly_box_mask_exact():
+    w = inputs.scaled_workload("batching", (20, 18, 16), m=12)
+    g = inputs.Grid(20, 18, 16, w.grid.h, mask_box=0.0105)
+    w = inputs.Workload(w.name, g, w.segments, w.freq_hz, w.tol, w.p)
+    Zo = dense(w)
+    Z64 = zbc.from_colmajor(gpu_assemble(w))
+    assert np.array_equal(Z64 == 0, Zo == 0)
+    assert (Zo == 0).any() and (Zo != 0).any()
+    assert rel_cols(Z64, Zo).max() < 1e-13
 
 
 def test_assembly_out_of_range_column_is_zero():

@@ -147,7 +147,7 @@ def test_entries_grow_linearly():
     assert xs.entries < 6 * g.nv / 2       # 6 tensors
     assert xs.max_check_err <= 3e-6       # an estimate of the error (about +-30 %)
     Zo = greens.assemble_columns(g.shape, g.h, w.segments.centre, w.segments.tangent, w.segments.length,
-                                 w.freq_hz, [1], mask_radius=g.mask_radius)
+                                 w.freq_hz, [1], mask_radius=g.mask_radius, mask_box=g.mask_box)
     tens, _ = h.tensors()
     for k in range(3):
         A = tucker.fold(Zo[k * g.nv:(k + 1) * g.nv, 0], g.shape)

@@ -38,7 +38,7 @@ def _c64(tens):
 def _handle(w, tol, V=None):
     g, s = w.grid, w.segments
     Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m),
-                                mask_radius=g.mask_radius)
+                                mask_radius=g.mask_radius, mask_box=g.mask_box)
     tens = _c64(tucker.compress_columns(Z, g.shape, 3, tol))
     return zbc.zbc_create_from_host(g, 3, tens, V), tens
 

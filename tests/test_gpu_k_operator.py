@@ -38,7 +38,7 @@ def _assemble(w, op, nq, dtype=torch.complex128, cols=None):
 def _oracle(w, op, nq):
     g, s = w.grid, w.segments
     return greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m),
-                                   mask_radius=g.mask_radius, operator=op, nq=nq)
+                                   mask_radius=g.mask_radius, mask_box=g.mask_box, operator=op, nq=nq)
 
 
 @pytest.mark.parametrize("op,nq", [("K", 1), ("K", 3), ("K", 8), ("N", 4), ("N", 1), ("K", 16)])
@@ -126,7 +126,7 @@ def test_pwl_assembly_matches_oracle(op, nq):
     g, s = w.grid, w.segments
     Zg = _assemble_q(w, op, nq, 12)
     Zo = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m), q=12,
-                                 mask_radius=g.mask_radius, operator=op, nq=nq)
+                                 mask_radius=g.mask_radius, mask_box=g.mask_box, operator=op, nq=nq)
     assert Zg.shape == Zo.shape == (12 * g.nv, s.m)
     for b in range(12):   # each block against its own scale (the linear blocks are ~100x smaller;
         blk = slice(b * g.nv, (b + 1) * g.nv)   # some columns of a block are exactly zero)

@@ -29,7 +29,7 @@ def rel_cols(a, b):
 def _handle(w, tol, V=None):
     g, s = w.grid, w.segments
     Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m),
-                                mask_radius=g.mask_radius)
+                                mask_radius=g.mask_radius, mask_box=g.mask_box)
     tens = tucker.compress_columns(Z, g.shape, 3, tol)
     tens = [[(t[0].astype(np.complex64).astype(np.complex128),
               [U.astype(np.complex64).astype(np.complex128) for U in t[1]]) for t in tj] for tj in tens]

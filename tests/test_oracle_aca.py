@@ -40,7 +40,7 @@ def _green_case(mask_radius=None):
     if mask_radius is not None:
         g = inputs.Grid(g.n1, g.n2, g.n3, g.h, mask_radius)
     Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, np.arange(s.m),
-                                mask_radius=g.mask_radius)
+                                mask_radius=g.mask_radius, mask_box=g.mask_box)
     return g, Z
 
 

@@ -21,7 +21,7 @@ def _planted(n, r, seed):
 def _green_tensor(w, e, k):
     g, s = w.grid, w.segments
     Z = greens.assemble_columns(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, [e],
-                                mask_radius=g.mask_radius)[:, 0]
+                                mask_radius=g.mask_radius, mask_box=g.mask_box)[:, 0]
     return tucker.fold(Z[k * g.nv:(k + 1) * g.nv], g.shape)
 
 
@@ -111,7 +111,7 @@ def test_green_source_indexes_the_column():
     g, s = w.grid, w.segments
     for k in range(3):
         A = _green_tensor(w, 1, k)
-        src = xt.green_source(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, 1, k, mask_radius=g.mask_radius)
+        src = xt.green_source(g.shape, g.h, s.centre, s.tangent, s.length, w.freq_hz, 1, k, mask_radius=g.mask_radius, mask_box=g.mask_box)
         i1, i2, i3 = np.meshgrid(np.arange(12), np.arange(10), np.arange(8), indexing="ij")
         assert np.array_equal(src(i1, i2, i3), A)
 

@@ -119,6 +119,38 @@ def test_mask_zeroes_outer_voxels():
         assert np.all(seg[~keep] == 0) and np.all(seg[keep] != 0)
 
 
+def test_box_mask_is_separable_and_keeps_tucker_ranks():
+    """The box mask drops exactly the voxels with max(|x|, |y|) > mask_box (a loop over voxels),
+    and, being a product of per-axis indicators, it leaves the multilinear ranks of a column's
+    tensor those of the unmasked field on the kept box, where a radial mask raises them."""
+    from oracle import tucker
+    g = inputs.Grid(16, 14, 6, 0.01, mask_box=0.045)
+    keep = greens.voxel_mask(*g.shape, g.h, 0.0, g.mask_box)
+    for v in range(g.nv):
+        i1, i2 = v % g.n1, (v // g.n1) % g.n2
+        x, y = (i1 - (g.n1 - 1) / 2.0) * g.h, (i2 - (g.n2 - 1) / 2.0) * g.h
+        assert keep[v] == (abs(x) <= g.mask_box and abs(y) <= g.mask_box)
+    assert 0 < keep.sum() < g.nv
+    c = np.array([[0.15, 0.02, 0.01]])
+    t = np.array([[0.0, 0.6, 0.8]])
+    z = greens.assemble_columns(g.shape, g.h, c, t, np.array([0.01]), 3e8, [0], mask_box=g.mask_box)
+    full = greens.assemble_columns(g.shape, g.h, c, t, np.array([0.01]), 3e8, [0])
+    assert np.array_equal(z[np.tile(keep, 3), 0], full[np.tile(keep, 3), 0])
+    assert np.all(z[~np.tile(keep, 3), 0] == 0)
+    i1 = np.abs((np.arange(g.n1) - (g.n1 - 1) / 2.0) * g.h) <= g.mask_box
+    i2 = np.abs((np.arange(g.n2) - (g.n2 - 1) / 2.0) * g.h) <= g.mask_box
+    for k in range(3):
+        A = tucker.fold(z[k * g.nv:(k + 1) * g.nv, 0], g.shape)
+        B = tucker.fold(full[k * g.nv:(k + 1) * g.nv, 0], g.shape)[np.ix_(i1, i2, np.arange(g.n3))]
+        _, _, ia = tucker.hosvd(A, 1e-6)
+        _, _, ib = tucker.hosvd(B, 1e-6)
+        assert tuple(ia["ranks"]) == tuple(ib["ranks"])
+    zr = greens.assemble_columns(g.shape, g.h, c, t, np.array([0.01]), 3e8, [0], mask_radius=g.mask_box)
+    _, _, ir = tucker.hosvd(tucker.fold(zr[:g.nv, 0], g.shape), 1e-6)
+    _, _, ib = tucker.hosvd(tucker.fold(z[:g.nv, 0], g.shape), 1e-6)
+    assert ir["ranks"][0] > ib["ranks"][0]
+
+
 # ------------------------------------------------------------------------------------------------
 # the K operator (Eq. nKt: curl of the single-layer potential) and the segment quadrature
 # ------------------------------------------------------------------------------------------------
