@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "mode1.cuh"
 
@@ -61,6 +62,17 @@ struct DcCol {
   int pad;
 };
 
+// What the copy warp needs of one chunk, in 128 bytes (one coalesced load of 32 words)
+struct __align__(16) DcChunk {
+  int j0, nc, z, k;     // first column, columns, sum of r1p, component
+  int r1p[kDcCols];
+  int64_t woff[kDcCols];
+  int64_t pre32;        // 32 x (sum of r1p over the component's columns before j0): the chunk's
+                        // U1 block within a (component, i1 group) block of u1g
+  int pad[2];
+};
+static_assert(sizeof(DcChunk) == 128, "one word per lane");
+
 struct DcCache {
   int ng1 = 0, NC = 0;
   std::vector<int> chbase;        // host: first chunk of each component (q + 1 entries)
@@ -69,7 +81,8 @@ struct DcCache {
   int max_rows = 0;               // largest sum of r1p over a chunk (sizes the stages)
   float2* u1g = nullptr;          // [k][g1][j][a/2][32][2]
   int64_t* u1off = nullptr;       // [(k ng1 + g1)(M + 1) + j]: start of column j's block (elements)
-  DcCol* cols = nullptr;          // [j q + k]
+  int64_t* u1base = nullptr;      // [k ng1 + g1]: start of a (component, i1 group) block
+  DcChunk* rec = nullptr;         // [chunk]
   int4* chunks = nullptr;         // [chunk]: (first column, columns, sum of r1p, component)
   int* d_chbase = nullptr;        // chbase on the device
   int* Ek = nullptr;              // [q]
@@ -82,7 +95,8 @@ void dc_release(DcCache* c) {
   if (!c) return;
   cudaFree(c->u1g);
   cudaFree(c->u1off);
-  cudaFree(c->cols);
+  cudaFree(c->u1base);
+  cudaFree(c->rec);
   cudaFree(c->chunks);
   cudaFree(c->d_chbase);
   cudaFree(c->Ek);
@@ -198,10 +212,29 @@ static int build_dc(Handle& h, cudaStream_t st) {
       }
       o[M] = off;
     }
+  std::vector<int64_t> u1base((size_t)q * ng1);
+  for (size_t kg = 0; kg < u1base.size(); ++kg) u1base[kg] = u1off[kg * (M + 1)];
+  std::vector<DcChunk> rec(dc->NC);
+  for (int c = 0; c < dc->NC; ++c) {
+    const int4 ch = dc->chunks_h[c];
+    DcChunk& r = rec[c];
+    std::memset(&r, 0, sizeof(r));
+    r.j0 = ch.x;
+    r.nc = ch.y;
+    r.z = ch.z;
+    r.k = ch.w;
+    for (int cc = 0; cc < ch.y; ++cc) {
+      const DcCol& col = cols[(int64_t)(ch.x + cc) * q + ch.w];
+      r.r1p[cc] = col.r1p;
+      r.woff[cc] = col.woff;
+    }
+    r.pre32 = u1off[(size_t)ch.w * ng1 * (M + 1) + ch.x] - u1off[(size_t)ch.w * ng1 * (M + 1)];
+  }
   float* d_bound = nullptr;
   cudaError_t e = cudaMalloc(&dc->u1g, sizeof(float2) * std::max<int64_t>(1, off));
   if (e == cudaSuccess) e = cudaMalloc(&dc->u1off, sizeof(int64_t) * u1off.size());
-  if (e == cudaSuccess) e = cudaMalloc(&dc->cols, sizeof(DcCol) * T);
+  if (e == cudaSuccess) e = cudaMalloc(&dc->u1base, sizeof(int64_t) * u1base.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dc->rec, sizeof(DcChunk) * dc->NC);
   if (e == cudaSuccess) e = cudaMalloc(&dc->chunks, sizeof(int4) * dc->NC);
   if (e == cudaSuccess) e = cudaMalloc(&dc->Ek, sizeof(int) * q);
   if (e == cudaSuccess) e = cudaMalloc(&dc->d_chbase, sizeof(int) * (q + 1));
@@ -210,7 +243,9 @@ static int build_dc(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&d_bound, sizeof(float) * T);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dc->u1off, u1off.data(), sizeof(int64_t) * u1off.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dc->cols, cols.data(), sizeof(DcCol) * T, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dc->u1base, u1base.data(), sizeof(int64_t) * u1base.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dc->rec, rec.data(), sizeof(DcChunk) * dc->NC, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dc->chunks, dc->chunks_h.data(), sizeof(int4) * dc->NC, cudaMemcpyHostToDevice, st);
   std::vector<float> bound(T);
@@ -246,7 +281,8 @@ static int build_dc(Handle& h, cudaStream_t st) {
     return ZBC_ECUDA;
   }
   dc->bytes = (int64_t)(sizeof(float2) * std::max<int64_t>(1, off) + sizeof(int64_t) * u1off.size() +
-                        sizeof(DcCol) * T + sizeof(int4) * dc->NC + sizeof(int) * (2 * q + 1));
+                        sizeof(int64_t) * u1base.size() + sizeof(DcChunk) * dc->NC + sizeof(int4) * dc->NC +
+                        sizeof(int) * (2 * q + 1));
   c->dc = dc;
   return ZBC_OK;
 }
@@ -329,8 +365,8 @@ __global__ void __launch_bounds__(256) dc_b_kernel(const float2* __restrict__ X,
 struct DcParams {
   const unsigned char* B;    // per call, [nsc][NC][2][2P][16] fp16
   const float2* u1g;
-  const int64_t* u1off;
-  const DcCol* cols;
+  const int64_t* u1base;
+  const DcChunk* rec;
   const int4* chunks;
   const int* chbase;         // device [q + 1]
   const float2* Wc;          // the decompression cache
@@ -413,54 +449,77 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
 
   if (warp == 8) {
     // ---------------- copy warp ----------------
-    if (lane == 0) {
-      uint32_t cnt = 0;
-      for (int64_t it = blockIdx.x; it < prm.nitems && !abort_flag; it += gridDim.x) {
-        int k, sc, b, g1;
-        dc_item(prm, it, k, sc, b, g1);
-        const int i23_0 = b * 4 * T;
-        const int rows = min(4 * T, prm.n23 - i23_0);
-        const int64_t* uo = prm.u1off + ((int64_t)k * prm.ng1 + g1) * (prm.M + 1);
-        const int c1 = prm.chbase[k + 1];
-        for (int c = prm.chbase[k]; c < c1 && !abort_flag; ++c, ++cnt) {
-          const int st = cnt % S;
-          if (cnt >= (uint32_t)S && (abort_flag || !tc::mbar_wait(&sempty[st], ((cnt / S) - 1) & 1))) {
-            abort_flag = 1;
-            break;
-          }
-          const int4 ch = prm.chunks[c];
-          unsigned char* sb = smem + (size_t)st * prm.stage_bytes;
-          const uint32_t ub = (uint32_t)(uo[ch.x + ch.y] - uo[ch.x]) * 8u;
-          const uint32_t wb = (uint32_t)rows * (uint32_t)ch.z * 8u;  // ch.z = the chunk's sum of r1p
-          const uint32_t bb = (uint32_t)(2 * N * 32);
-          // the chunk's metadata first (plain stores, released by the arrive below)
-          DcHdr* hd = reinterpret_cast<DcHdr*>(sb + prm.h_off);
-          {
-            uint32_t wo = 0, uof = 0;
-            for (int cc = 0; cc < ch.y; ++cc) {
-              const int r1p = prm.cols[(int64_t)(ch.x + cc) * prm.q + k].r1p;
-              hd->r1p[cc] = r1p;
-              hd->uo[cc] = (int)(uof / 16u);
-              hd->wo[cc] = (int)(wo / 16u);
-              wo += (uint32_t)(4 * T) * r1p * 8u;
-              uof += (uint32_t)r1p * 32u * 8u;
-            }
-            hd->nc = ch.y;
-          }
-          mbar_arrive_expect_tx(&sfull[st], ub + wb + bb);
-          bulk_g2s(sb, prm.u1g + uo[ch.x], ub, &sfull[st]);
-          uint32_t wo = prm.w_off;
-          for (int cc = 0; cc < ch.y; ++cc) {
-            const DcCol col = prm.cols[(int64_t)(ch.x + cc) * prm.q + k];
-            bulk_g2s(sb + wo, prm.Wc + col.woff + (int64_t)i23_0 * col.r1p, (uint32_t)rows * col.r1p * 8u, &sfull[st]);
-            wo += (uint32_t)(4 * T) * col.r1p * 8u;
-          }
+    // The lanes share each chunk: its 128-byte record is one coalesced load (issued a chunk ahead,
+    // so that no global-memory latency sits between two chunks), lane cc < nc writes column cc's
+    // header entries and issues its W copy, lane 0 waits for the free stage, sets the barrier's
+    // transaction count and issues the U1 and B copies.
+    constexpr unsigned kAll = 0xffffffffu;
+    uint32_t cnt = 0;
+    bool stop = false;
+    for (int64_t it = blockIdx.x; it < prm.nitems && !stop; it += gridDim.x) {
+      int k, sc, b, g1;
+      dc_item(prm, it, k, sc, b, g1);
+      const int i23_0 = b * 4 * T;
+      const int rows = min(4 * T, prm.n23 - i23_0);
+      const int64_t ubase = prm.u1base[(int64_t)k * prm.ng1 + g1];
+      const int c0 = prm.chbase[k], c1 = prm.chbase[k + 1];
+      int word = reinterpret_cast<const int*>(prm.rec + c0)[lane];
+      for (int c = c0; c < c1; ++c, ++cnt) {
+        const int st = cnt % S;
+        const int wnext = c + 1 < c1 ? reinterpret_cast<const int*>(prm.rec + c + 1)[lane] : 0;
+        bool ok = true;
+        if (lane == 0) ok = !abort_flag && (cnt < (uint32_t)S || tc::mbar_wait_idle(&sempty[st], ((cnt / S) - 1) & 1));
+        if (!__shfl_sync(kAll, ok, 0)) {
+          if (lane == 0) abort_flag = 1;
+          stop = true;
+          break;
+        }
+        // record words: 1 nc, 2 sum of r1p, 4 + cc r1p, 12 + 2 cc / 13 + 2 cc woff, 28 / 29 pre32
+        const int nc = __shfl_sync(kAll, word, 1);
+        const int z = __shfl_sync(kAll, word, 2);
+        const int cl = lane & (kDcCols - 1);
+        const int r1p = __shfl_sync(kAll, word, 4 + cl);
+        const uint32_t wlo = (uint32_t)__shfl_sync(kAll, word, 12 + 2 * cl);
+        const uint32_t whi = (uint32_t)__shfl_sync(kAll, word, 13 + 2 * cl);
+        const uint32_t plo = (uint32_t)__shfl_sync(kAll, word, 28);
+        const uint32_t phi = (uint32_t)__shfl_sync(kAll, word, 29);
+        const bool mine = lane < nc;
+        int pre = mine ? r1p : 0;  // inclusive sum of r1p over lanes 0 .. lane, then exclusive
+#pragma unroll
+        for (int o = 1; o < kDcCols; o <<= 1) {
+          const int v = __shfl_up_sync(kAll, pre, o);
+          if (lane >= o) pre += v;
+        }
+        pre -= mine ? r1p : 0;
+        unsigned char* sb = smem + (size_t)st * prm.stage_bytes;
+        DcHdr* hd = reinterpret_cast<DcHdr*>(sb + prm.h_off);
+        if (mine) {
+          hd->r1p[lane] = r1p;
+          hd->uo[lane] = pre * 16;     // float4 units: 32 rows x r1p complex64 per column
+          hd->wo[lane] = pre * 2 * T;  // float4 units: 4T rows x r1p complex64 per column
+        }
+        if (lane == 0) hd->nc = nc;
+        __threadfence_block();
+        __syncwarp();  // the header stores come before lane 0's arrive (which releases them)
+        const uint32_t ub = (uint32_t)z * 32u * 8u, wb = (uint32_t)rows * (uint32_t)z * 8u;
+        const uint32_t bb = (uint32_t)(2 * N * 32);
+        if (lane == 0) mbar_arrive_expect_tx(&sfull[st], ub + wb + bb);
+        __syncwarp();  // the transaction count is set before any copy is issued
+        if (lane == 0) {
+          const int64_t pre32 = (int64_t)(((uint64_t)phi << 32) | plo);
+          bulk_g2s(sb, prm.u1g + ubase + pre32, ub, &sfull[st]);
           bulk_g2s(sb + prm.b_off, prm.B + ((int64_t)sc * prm.NC + c) * bb, bb, &sfull[st]);
         }
+        if (mine) {
+          const int64_t woff = (int64_t)(((uint64_t)whi << 32) | wlo);
+          bulk_g2s(sb + prm.w_off + (uint32_t)pre * (uint32_t)(4 * T) * 8u, prm.Wc + woff + (int64_t)i23_0 * r1p,
+                   (uint32_t)rows * (uint32_t)r1p * 8u, &sfull[st]);
+        }
+        word = wnext;
       }
-      if (abort_flag)  // let the copies in flight land before the CTA exits
-        for (uint32_t c = cnt > (uint32_t)S ? cnt - S : 0; c < cnt; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
     }
+    if (lane == 0 && abort_flag)  // let the copies in flight land before the CTA exits
+      for (uint32_t c = cnt > (uint32_t)S ? cnt - S : 0; c < cnt; ++c) tc::mbar_wait(&sfull[c % S], (c / S) & 1);
     __syncwarp();
   } else if (warp == 9) {
     // ---------------- MMA warp ----------------
@@ -474,8 +533,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
         for (int cl = 0; cl < nch && !abort_flag; ++cl, ++gc) {
           const bool first = cl % kDcSeg == 0, last = cl % kDcSeg == kDcSeg - 1 || cl == nch - 1;
           const int st = gc % S, ab = gc & 1;
-          bool ok = !(first && gs >= 1) || tc::mbar_wait(&dempty, (gs - 1) & 1);
-          ok = ok && tc::mbar_wait(&sfull[st], (gc / S) & 1) && tc::mbar_wait(&afull[ab], (gc >> 1) & 1);
+          bool ok = !(first && gs >= 1) || tc::mbar_wait_idle(&dempty, (gs - 1) & 1);
+          ok = ok && tc::mbar_wait_idle(&sfull[st], (gc / S) & 1) && tc::mbar_wait_idle(&afull[ab], (gc >> 1) & 1);
           if (!ok) {
             abort_flag = 1;
             break;
@@ -587,19 +646,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
             const int n2 = hd->r1p[cc] / 2;
             const float4* U = Us + hd->uo[cc];                       // pair a2 at U[32 a2]
             const float4* W = Ws + hd->wo[cc] + gb * n2;             // tile t at W[4 n2 t + a2]
-            float4 u = U[0];
-            float4 wv[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) wv[t] = W[4 * n2 * t];
-            for (int a2 = 0; a2 < n2; ++a2) {
-              float4 un = u, wn[T];
-#pragma unroll
-              for (int t = 0; t < T; ++t) wn[t] = wv[t];
-              if (a2 + 1 < n2) {
-                un = U[32 * (a2 + 1)];
-#pragma unroll
-                for (int t = 0; t < T; ++t) wn[t] = W[4 * n2 * t + a2 + 1];
-              }
+            // two register sets, loaded alternately one rank pair ahead of their use
+            auto macc = [&](const float4& u, const float4 (&wv)[T]) {
 #pragma unroll
               for (int t = 0; t < T; ++t) {
                 ae[t].x = fmaf(u.x, wv[t].x, fmaf(-u.y, wv[t].y, ae[t].x));
@@ -607,10 +655,25 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
                 ao[t].x = fmaf(u.z, wv[t].z, fmaf(-u.w, wv[t].w, ao[t].x));
                 ao[t].y = fmaf(u.z, wv[t].w, fmaf(u.w, wv[t].z, ao[t].y));
               }
-              u = un;
+            };
+            float4 u0 = U[0], u1;
+            float4 w0[T], w1[T];
 #pragma unroll
-              for (int t = 0; t < T; ++t) wv[t] = wn[t];
+            for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t];
+            int a2 = 0;
+            for (; a2 + 1 < n2; a2 += 2) {
+              u1 = U[32 * (a2 + 1)];
+#pragma unroll
+              for (int t = 0; t < T; ++t) w1[t] = W[4 * n2 * t + a2 + 1];
+              macc(u0, w0);
+              if (a2 + 2 < n2) {
+                u0 = U[32 * (a2 + 2)];
+#pragma unroll
+                for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t + a2 + 2];
+              }
+              macc(u1, w1);
             }
+            if (a2 < n2) macc(u0, w0);  // an odd number of rank pairs
           }
 #pragma unroll
           for (int t = 0; t < T; ++t) {
@@ -737,8 +800,8 @@ static int matvec_dc_p(Handle& h, const float2* X, int64_t ldx, int p, float2* Y
   count_launch(2);
   prm.B = B;
   prm.u1g = dc.u1g;
-  prm.u1off = dc.u1off;
-  prm.cols = dc.cols;
+  prm.u1base = dc.u1base;
+  prm.rec = dc.rec;
   prm.chunks = dc.chunks;
   prm.chbase = dc.d_chbase;
   prm.Wc = h.cache->data;

@@ -132,6 +132,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// The same wait for warps that have nothing else to issue meanwhile (a copy or MMA warp): each
+// try_wait may suspend the thread for up to 1 us while the phase is pending, so the wait takes few
+// issue slots from the warps that share its scheduler; at most max_iter tries (about 4 s).
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* mbar, uint32_t parity, uint32_t max_iter = 4000000u) {
+  const uint32_t a = smem_u32(mbar);
+  for (uint32_t it = 0; it < max_iter; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "r"(1000u)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // byte offset of (row r, 16-byte K-chunk kc) in the canonical layout with KB chunks per row
 __host__ __device__ __forceinline__ uint32_t core_off(uint32_t r, uint32_t kc, uint32_t KB) {
   return (r >> 3) * (KB * 128u) + kc * 128u + (r & 7u) * 16u;

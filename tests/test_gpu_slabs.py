@@ -43,13 +43,14 @@ def _handle(shape, m, aca):
 
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("aca", [False, True])
-@pytest.mark.parametrize("prec", ["fp32", "mode1"])
+@pytest.mark.parametrize("prec", ["fp32", "mode1", "dc"])
 def test_slab_handles_reproduce_both_products(world, aca, prec):
     shape = (40, 18, 10)                     # slabs of 5 + 5 and of 3 + 3 + 4 planes
     h, g = _handle(shape, 12, aca)
     inf = h.info()
     p = 5
-    fw, aj = (zbc.FP32_SIMT, zbc.FP32_SIMT) if prec == "fp32" else (zbc.TC_MODE1, zbc.TC_MODE1)
+    fw, aj = {"fp32": (zbc.FP32_SIMT, zbc.FP32_SIMT), "mode1": (zbc.TC_MODE1, zbc.TC_MODE1),
+              "dc": (zbc.TC_DC, zbc.TC_MODE1)}[prec]
     X = inputs.cn01((inf.m, p), seed=1).astype(np.complex64)
     Phi = inputs.cn01((3 * g.nv, p), seed=2).astype(np.complex64)
     tens, V = h.tensors()
