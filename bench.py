@@ -550,8 +550,9 @@ def run_workload(name, args, zbc, torch, inputs, ws, rank, local, peaks, measure
     """Build the named workload's handle, measure its products and (rank 0) check them against the
     oracle and time the oracle.  Returns the JSON fields of this workload."""
     w = inputs.workload(name)
-    if args.columns:
-        w = inputs.scaled_workload(name, w.grid.shape, m=args.columns)
+    if args.columns or args.n3:
+        n1, n2, n3 = w.grid.shape
+        w = inputs.scaled_workload(name, (n1, n2, args.n3 or n3), m=args.columns or None)
     g = w.grid
     if w.aca:
         h, t_build, build = build_randomized(w, zbc, torch, inputs)
@@ -639,7 +640,7 @@ def run_zbc(args):
     }
     line.update(head)
     line["peaks_measured"] = dict(measured, source="torch.matmul 8192^3 in this run, best of 6")
-    if not args.no_extras and ws == 1 and not args.columns:
+    if not args.no_extras and ws == 1 and not args.columns and not args.n3:
         # the other workloads ride along as sub-objects, each started only while the run is inside
         # its time budget (a skipped one says so)
         extra = {}
@@ -647,8 +648,8 @@ def run_zbc(args):
         if args.workload != "precision":
             jobs.append(("precision", lambda: dict(run_workload("precision", args, zbc, torch, inputs, ws, rank, local,
                                                                 peaks, measured, baseline=False), unit=UNIT)))
-        jobs += [("batching", lambda: batching(zbc, torch, inputs)),
-                 ("learned", lambda: compression(zbc, torch, inputs))]
+        jobs += [("learned", lambda: compression(zbc, torch, inputs)),
+                 ("batching", lambda: batching(zbc, torch, inputs))]
         for name, job in jobs:
             used = time.time() - T_START
             if used > args.extras_budget:
@@ -759,7 +760,8 @@ def compression(zbc, torch, inputs, ntrain=256, ntest=256, batch=128):
     compressed by (a) truncated HOSVD, (b) the randomized Tucker with the MLP's widths, (c) the
     randomized Tucker with one fixed width for every tensor, the training set's largest rank + 4
     (the method without the network), and (d) a fixed width equal to the MLP's mean width (the
-    same sketch budget spread evenly).  Time per column, fallback rate, errors, mean ranks."""
+    same sketch budget spread evenly); (b) also with 8 instead of 4 oversampling columns.  Time per
+    column, fallback rate, errors, mean ranks."""
     w = inputs.workload("learned")
     g, s = w.grid, w.segments
     perm = np.random.default_rng(7).permutation(s.m)
@@ -797,7 +799,7 @@ def compression(zbc, torch, inputs, ntrain=256, ntest=256, batch=128):
     models = {"fixed_max": zbc.rank_model(sk, lmax, fixed_width=fixed_max),
               "fixed_mean": zbc.rank_model(sk, lmax, fixed_width=fixed_mean)}
     res = {k: {"s": 0.0, "fallback": 0, "tensors": 0, "err": 0.0, "ranks": []}
-           for k in ("hosvd", "learned", "fixed_max", "fixed_mean")}
+           for k in ("hosvd", "learned", "learned_os8", "fixed_max", "fixed_mean")}
     for b0 in range(0, ntest, batch):
         cols = test[b0:b0 + batch]
         Z = assemble(cols)
@@ -807,9 +809,10 @@ def compression(zbc, torch, inputs, ntrain=256, ntest=256, batch=128):
             t0 = time.perf_counter()
             if k == "hosvd":
                 hh, st = zbc.tucker_compress(Z, g, w.tol)
-            elif k == "learned":
+            elif k.startswith("learned"):
+                os_ = 8 if k == "learned_os8" else 4
                 hh, st = zbc.tucker_compress(Z, g, w.tol, method=zbc.RANDOMIZED_LEARNED,
-                                             model=zbc.rank_model(sk, lmax, mlp=model, features=feats, oversample=4))
+                                             model=zbc.rank_model(sk, lmax, mlp=model, features=feats, oversample=os_))
             else:
                 hh, st = zbc.tucker_compress(Z, g, w.tol, method=zbc.RANDOMIZED_FIXED, model=models[k])
             torch.cuda.synchronize()
@@ -1014,7 +1017,7 @@ def main():
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extras-budget", type=float, default=900.0,
+    ap.add_argument("--extras-budget", type=float, default=700.0,
                     help="seconds since the start after which the ride-along workloads are skipped")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload (no precision / batching / learned sub-objects)")
@@ -1022,6 +1025,8 @@ def main():
                     help="compression from fibres (cross-Tucker) vs assembly + HOSVD instead of the products")
     ap.add_argument("--columns", type=int, default=0,
                     help="keep only N segments (smaller case for profiler captures; no extras)")
+    ap.add_argument("--n3", type=int, default=0,
+                    help="keep only N planes of i3 (smaller case for profiler captures; no extras)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -633,52 +633,109 @@ __global__ void __launch_bounds__(kDcThreads, 1) matvec_dc_kernel(const DcParams
         const int nc = hd->nc;
         const float4* __restrict__ Us = reinterpret_cast<const float4*>(sb) + gi1;
         const float4* __restrict__ Ws = reinterpret_cast<const float4*>(sb + prm.w_off);
+        // T <= 2: the warpgroup's four columns advance together, one rank pair a2 per step: a step
+        // loads the U1 pair and the T W pairs of each column, then does the four columns' FMAs, so
+        // four independent load / FMA chains are in flight (a column's own chain is only r1 / 2
+        // long).  T = 4: one column after the other, each with its next rank pair's operands loaded
+        // during the current pair's FMAs (measured faster there: four columns of T = 4 need more
+        // registers than the launch leaves).  Per column, even and odd a accumulate separately,
+        // each over a in increasing order, in both forms.
         float zr[T][4], zi[T][4];
+        if constexpr (T <= 2) {
+          constexpr int G = 4;
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const int cc = 4 * hg + c4;
-          // even and odd a accumulate in separate chains; the next a pair's operands are loaded
-          // before the current pair's FMAs
-          float2 ae[T], ao[T];
+          for (int g0 = 0; g0 < 4; g0 += G) {
+            float2 ae[G][T], ao[G][T];
+            int n2c[G];
+            const float4* Uc[G];
+            const float4* Wcol[G];
+            int n2max = 0;
 #pragma unroll
-          for (int t = 0; t < T; ++t) ae[t] = ao[t] = make_float2(0.f, 0.f);
-          if (cc < nc) {
-            const int n2 = hd->r1p[cc] / 2;
-            const float4* U = Us + hd->uo[cc];                       // pair a2 at U[32 a2]
-            const float4* W = Ws + hd->wo[cc] + gb * n2;             // tile t at W[4 n2 t + a2]
-            // two register sets, loaded alternately one rank pair ahead of their use
-            auto macc = [&](const float4& u, const float4 (&wv)[T]) {
+            for (int c = 0; c < G; ++c) {
+              const int cc = 4 * hg + g0 + c;
+              const bool on = cc < nc;
+              n2c[c] = on ? hd->r1p[cc] / 2 : 0;
+              Uc[c] = Us + (on ? hd->uo[cc] : 0);                      // pair a2 at Uc[32 a2]
+              Wcol[c] = Ws + (on ? hd->wo[cc] : 0) + gb * n2c[c];      // tile t at Wcol[4 n2 t + a2]
+              n2max = max(n2max, n2c[c]);
+#pragma unroll
+              for (int t = 0; t < T; ++t) ae[c][t] = ao[c][t] = make_float2(0.f, 0.f);
+            }
+            for (int a2 = 0; a2 < n2max; ++a2) {
+              float4 u[G], wv[G][T];
+#pragma unroll
+              for (int c = 0; c < G; ++c)
+                if (a2 < n2c[c]) {
+                  u[c] = Uc[c][32 * a2];
+#pragma unroll
+                  for (int t = 0; t < T; ++t) wv[c][t] = Wcol[c][4 * n2c[c] * t + a2];
+                }
+#pragma unroll
+              for (int c = 0; c < G; ++c)
+                if (a2 < n2c[c]) {
+#pragma unroll
+                  for (int t = 0; t < T; ++t) {
+                    const float4 w = wv[c][t];
+                    ae[c][t].x = fmaf(u[c].x, w.x, fmaf(-u[c].y, w.y, ae[c][t].x));
+                    ae[c][t].y = fmaf(u[c].x, w.y, fmaf(u[c].y, w.x, ae[c][t].y));
+                    ao[c][t].x = fmaf(u[c].z, w.z, fmaf(-u[c].w, w.w, ao[c][t].x));
+                    ao[c][t].y = fmaf(u[c].z, w.w, fmaf(u[c].w, w.z, ao[c][t].y));
+                  }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c)
 #pragma unroll
               for (int t = 0; t < T; ++t) {
-                ae[t].x = fmaf(u.x, wv[t].x, fmaf(-u.y, wv[t].y, ae[t].x));
-                ae[t].y = fmaf(u.x, wv[t].y, fmaf(u.y, wv[t].x, ae[t].y));
-                ao[t].x = fmaf(u.z, wv[t].z, fmaf(-u.w, wv[t].w, ao[t].x));
-                ao[t].y = fmaf(u.z, wv[t].w, fmaf(u.w, wv[t].z, ao[t].y));
+                zr[t][g0 + c] = (ae[c][t].x + ao[c][t].x) * fz;
+                zi[t][g0 + c] = (ae[c][t].y + ao[c][t].y) * fz;
               }
-            };
-            float4 u0 = U[0], u1;
-            float4 w0[T], w1[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t];
-            int a2 = 0;
-            for (; a2 + 1 < n2; a2 += 2) {
-              u1 = U[32 * (a2 + 1)];
-#pragma unroll
-              for (int t = 0; t < T; ++t) w1[t] = W[4 * n2 * t + a2 + 1];
-              macc(u0, w0);
-              if (a2 + 2 < n2) {
-                u0 = U[32 * (a2 + 2)];
-#pragma unroll
-                for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t + a2 + 2];
-              }
-              macc(u1, w1);
-            }
-            if (a2 < n2) macc(u0, w0);  // an odd number of rank pairs
           }
+        } else {
 #pragma unroll
-          for (int t = 0; t < T; ++t) {
-            zr[t][c4] = (ae[t].x + ao[t].x) * fz;
-            zi[t][c4] = (ae[t].y + ao[t].y) * fz;
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const int cc = 4 * hg + c4;
+            float2 ae[T], ao[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) ae[t] = ao[t] = make_float2(0.f, 0.f);
+            if (cc < nc) {
+              const int n2 = hd->r1p[cc] / 2;
+              const float4* U = Us + hd->uo[cc];                       // pair a2 at U[32 a2]
+              const float4* W = Ws + hd->wo[cc] + gb * n2;             // tile t at W[4 n2 t + a2]
+              // two register sets, loaded alternately one rank pair ahead of their use
+              auto macc = [&](const float4& u, const float4 (&wv)[T]) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                  ae[t].x = fmaf(u.x, wv[t].x, fmaf(-u.y, wv[t].y, ae[t].x));
+                  ae[t].y = fmaf(u.x, wv[t].y, fmaf(u.y, wv[t].x, ae[t].y));
+                  ao[t].x = fmaf(u.z, wv[t].z, fmaf(-u.w, wv[t].w, ao[t].x));
+                  ao[t].y = fmaf(u.z, wv[t].w, fmaf(u.w, wv[t].z, ao[t].y));
+                }
+              };
+              float4 u0 = U[0], u1;
+              float4 w0[T], w1[T];
+#pragma unroll
+              for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t];
+              int a2 = 0;
+              for (; a2 + 1 < n2; a2 += 2) {
+                u1 = U[32 * (a2 + 1)];
+#pragma unroll
+                for (int t = 0; t < T; ++t) w1[t] = W[4 * n2 * t + a2 + 1];
+                macc(u0, w0);
+                if (a2 + 2 < n2) {
+                  u0 = U[32 * (a2 + 2)];
+#pragma unroll
+                  for (int t = 0; t < T; ++t) w0[t] = W[4 * n2 * t + a2 + 2];
+                }
+                macc(u1, w1);
+              }
+              if (a2 < n2) macc(u0, w0);  // an odd number of rank pairs
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+              zr[t][c4] = (ae[t].x + ao[t].x) * fz;
+              zi[t][c4] = (ae[t].y + ao[t].y) * fz;
+            }
           }
         }
         // A pieces: Re Z of columns 4 hg .. 4 hg + 3 at K = 8 hg .. 8 hg + 3, Im Z at K = 8 hg + 4 ..,
