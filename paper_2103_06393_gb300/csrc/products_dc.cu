@@ -41,7 +41,7 @@ namespace zbc {
 
 constexpr int kDcCols = 8;        // columns per chunk: the MMA's K = 16 = (Re, Im) x 8
 constexpr int kDcRows = 128;      // rank rows (sum of r1p) per chunk: the stage's U1 capacity
-constexpr int kDcSeg = 8;         // chunks per tensor-core accumulation before a fold into S
+constexpr int kDcSeg = 16;        // chunks per tensor-core accumulation before a fold into S
 constexpr int kDcMaxStages = 6;
 constexpr int kDcThreads = 32 * 10;  // 8 generator / fold warps, copy warp, MMA warp
 constexpr int kDcShift = 14;      // fp16 hi terms below 2^kDcShift
