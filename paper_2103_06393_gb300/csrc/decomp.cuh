@@ -122,8 +122,12 @@ struct DecompCache {
   Mode1Cache* mode1 = nullptr;
   DcCache* dc = nullptr;    // operands of the decompress-and-contract tensor-core forward (products_dc.cu)
   int64_t bytes = 0;        // device bytes held (W, U1, descriptors, fp16 copies; not mode1's)
+  int64_t half_bytes = 0;   // the part of bytes held by half / d_half
 };
 int build_decomp_cache(Handle& h, cudaStream_t st);
 int build_half_cache(Handle& h, cudaStream_t st);
+void half_release(DecompCache* c);         // the fp16 U1 blocks (rebuilt on the next use)
+void mode1_fwd_release(Mode1Cache* c);     // the mode-1 forward's operands (rebuilt on the next use)
+void dc_release(DcCache* c);
 
 }  // namespace zbc

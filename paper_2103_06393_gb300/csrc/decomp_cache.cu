@@ -25,6 +25,16 @@ void cache_release(DecompCache* c) {
   delete c;
 }
 
+void half_release(DecompCache* c) {
+  if (!c) return;
+  if (c->half) cudaFree(c->half);
+  if (c->d_half) cudaFree(c->d_half);
+  c->half = nullptr;
+  c->d_half = nullptr;
+  c->bytes -= c->half_bytes;
+  c->half_bytes = 0;
+}
+
 // one CTA per (i3, tensor): P[a][b] = sum_c G[a,b,c] U3[i3,c]; W[i3][i2][a] = sum_b P[a][b] U2[i2,b]
 __global__ void __launch_bounds__(256) build_w_kernel(const float2* __restrict__ pool, const TensorDesc* __restrict__ desc,
                                                       const CacheDesc* __restrict__ cdesc, int n1, int n2, int n3,
@@ -211,7 +221,10 @@ int build_half_cache(Handle& h, cudaStream_t st) {
   }
   cudaError_t e = cudaMalloc(&c->half, std::max<int64_t>(16, off));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_half, sizeof(HalfDesc) * std::max(1, T));
-  if (e == cudaSuccess) c->bytes += (int64_t)(std::max<int64_t>(16, off) + sizeof(HalfDesc) * std::max(1, T));
+  if (e == cudaSuccess) {
+    c->half_bytes = (int64_t)(std::max<int64_t>(16, off) + sizeof(HalfDesc) * std::max(1, T));
+    c->bytes += c->half_bytes;
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_half, hd.data(), sizeof(HalfDesc) * T, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     for (int t0 = 0; t0 < T; t0 += 65535) {
@@ -229,10 +242,7 @@ int build_half_cache(Handle& h, cudaStream_t st) {
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    if (c->half) cudaFree(c->half);
-    if (c->d_half) cudaFree(c->d_half);
-    c->half = nullptr;
-    c->d_half = nullptr;
+    half_release(c);
     set_error("fp16 operand cache build failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
   }

@@ -45,6 +45,7 @@ struct Mode1Cache {
   int2* chunkinfo = nullptr;  // [chunk] (first column, number of columns)
   int8_t* jtab = nullptr;     // [chunk][32] column of each row minus the chunk's first column
   int64_t bytes = 0;          // device bytes held by the operands above
+  int64_t fwd_bytes = 0;      // the part of bytes held by the forward operands
 };
 
 int build_mode1_cache(Handle& h, cudaStream_t st);

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "decomp.cuh"
 #include "zbc_internal.cuh"
 
 namespace zbc {
@@ -88,6 +89,31 @@ extern "C" int zbc_rmatvec(const zbc_handle* hh, const void* Phi, int64_t ldphi,
   if (prec == ZBC_AUTO) prec = h.tune_adj_prec[cls] >= 0 ? (zbc_precision)h.tune_adj_prec[cls] : ZBC_FP32_SIMT;
   return rmatvec_impl(h, (const float2*)Phi, ldphi, p, (float2*)Psi, ldpsi, prec, h.tune_adj_warps[cls],
                       (cudaStream_t)stream);
+}
+
+// The per-handle operands of the forms that no tuned right-hand-side class selects (untuned
+// classes fall back to BF16X3 or FP32_SIMT, which need none of them) are freed; a later call of
+// such a form builds them again.  The decompression cache itself is kept.
+static void release_unused_operands(Handle& h) {
+  DecompCache* c = h.cache;
+  if (!c) return;
+  bool m1f = false, m1a = false, dc = false, tc2 = false;
+  for (int i = 0; i < Handle::kPClasses; ++i) {
+    m1f = m1f || h.tune_fwd_prec[i] == ZBC_TC_MODE1;
+    dc = dc || h.tune_fwd_prec[i] == ZBC_TC_DC;
+    tc2 = tc2 || h.tune_fwd_prec[i] == ZBC_TC2;
+    m1a = m1a || h.tune_adj_prec[i] == ZBC_TC_MODE1;
+  }
+  if (c->mode1 && !m1f) mode1_fwd_release(c->mode1);
+  if (c->mode1 && !m1f && !m1a) {
+    mode1_release(c->mode1);
+    c->mode1 = nullptr;
+  }
+  if (c->dc && !dc) {
+    dc_release(c->dc);
+    c->dc = nullptr;
+  }
+  if (!tc2) half_release(c);
 }
 
 extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_ms_host) {
@@ -179,6 +205,7 @@ extern "C" int zbc_tune(zbc_handle* hh, int p, zbc_stream stream, float* times_m
   h.tune_adj_warps[cls] = (int8_t)(t[NF + 1] < t[NF] ? 9 : 6);
   if (times_ms_host)
     for (int i = 0; i < NV; ++i) times_ms_host[i] = t[i];
+  release_unused_operands(h);
   return ZBC_OK;
 }
 

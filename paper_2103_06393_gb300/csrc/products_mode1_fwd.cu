@@ -134,6 +134,18 @@ __global__ void __launch_bounds__(256) m1f_b_kernel(const float2* __restrict__ p
   *reinterpret_cast<uint4*>(blk + term) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+void mode1_fwd_release(Mode1Cache* c) {
+  if (!c) return;
+  for (void** ptr : {(void**)&c->Bf, (void**)&c->Wc, (void**)&c->ew, (void**)&c->chunkinfo, (void**)&c->jtab,
+                     (void**)&c->d_chbase}) {
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+  }
+  c->bytes -= c->fwd_bytes;
+  c->fwd_bytes = 0;
+  c->fwd = false;
+}
+
 static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   ZBC_TRY(build_mode1_cache(h, st));
   Mode1Cache& mc = *h.cache->mode1;
@@ -176,9 +188,11 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&mc.chunkinfo, sizeof(int2) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&mc.jtab, (size_t)NC * kFwdChunk);
   if (e == cudaSuccess) e = cudaMalloc(&mc.d_chbase, sizeof(int) * (q + 1));
-  if (e == cudaSuccess)
-    mc.bytes += (int64_t)(sizeof(uint32_t) * bwords + sizeof(float2) * wc_elems + sizeof(int) * (size_t)q * n23p +
-                          sizeof(int2) * NC + (size_t)NC * kFwdChunk + sizeof(int) * (q + 1));
+  if (e == cudaSuccess) {
+    mc.fwd_bytes = (int64_t)(sizeof(uint32_t) * bwords + sizeof(float2) * wc_elems + sizeof(int) * (size_t)q * n23p +
+                             sizeof(int2) * NC + (size_t)NC * kFwdChunk + sizeof(int) * (q + 1));
+    mc.bytes += mc.fwd_bytes;
+  }
   if (e == cudaSuccess) e = cudaMalloc(&d_row0, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_nr, sizeof(int) * NC);
   if (e == cudaSuccess) e = cudaMalloc(&d_ck, sizeof(int) * NC);
@@ -209,11 +223,7 @@ static int build_mode1_fwd(Handle& h, cudaStream_t st) {
   for (void* ptr : {(void*)d_row0, (void*)d_nr, (void*)d_ck, (void*)d_gbase, (void*)d_nrows})
     if (ptr) cudaFree(ptr);
   if (e != cudaSuccess) {  // leave the cache as it was, so that a later call can build it again
-    for (void** ptr : {(void**)&mc.Bf, (void**)&mc.Wc, (void**)&mc.ew, (void**)&mc.chunkinfo, (void**)&mc.jtab,
-                       (void**)&mc.d_chbase}) {
-      if (*ptr) cudaFree(*ptr);
-      *ptr = nullptr;
-    }
+    mode1_fwd_release(&mc);
     set_error("mode-1 forward operand build failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ZBC_ENOMEM : ZBC_ECUDA;
   }

@@ -53,6 +53,35 @@ def test_tune_then_auto_matches_oracle(p):
     assert _rel(zbc.from_colmajor(Psi), products.rmatvec(tens, g.shape, Phi)) < RTOL
 
 
+def test_tune_releases_operands_of_unselected_forms():
+    """zbc_tune frees the per-handle operands of the forms it did not select; a later call of such a
+    form builds them again and gives the same bits as before."""
+    h, tens, g = _handle()
+    p = 5
+    X = zbc.to_colmajor(inputs.cn01((len(tens), p), seed=7).astype(np.complex64))
+    outs = {}
+    for code in (zbc.TC_MODE1, zbc.TC_DC, zbc.TC2):
+        Y = zbc.colmajor(3 * g.nv, p, torch.complex64)
+        zbc.zbc_matvec(h, X, Y, code)
+        outs[code] = Y.clone()
+    Phi = zbc.to_colmajor(inputs.cn01((3 * g.nv, p), seed=8).astype(np.complex64))
+    Psi = zbc.colmajor(len(tens), p, torch.complex64)
+    zbc.zbc_rmatvec(h, Phi, Psi, zbc.TC_MODE1)
+    zbc.zbc_product_status(h)
+    before = h.device_bytes()["caches"]
+    t = zbc.zbc_tune(h, p)
+    fwd = min((k for k in t if k.startswith("fwd_")), key=lambda k: t[k])
+    after = h.device_bytes()["caches"]
+    # at most one of the three forward forms' operands stays
+    assert after < before, (before, after, fwd)
+    for code in (zbc.TC_MODE1, zbc.TC_DC, zbc.TC2):
+        Y = zbc.colmajor(3 * g.nv, p, torch.complex64)
+        zbc.zbc_matvec(h, X, Y, code)
+        zbc.zbc_product_status(h)
+        assert torch.equal(Y, outs[code]), code
+    assert h.device_bytes()["caches"] >= before
+
+
 def test_adjoint_rejects_tensor_core_forms():
     h, tens, g = _handle(n=(8, 8, 8), m=3)
     Phi = zbc.colmajor(3 * g.nv, 2, torch.complex64)
