@@ -2,18 +2,20 @@
 compressed coupling matrix.
 
 Default workload ("large"): 320 x 320 x 256 voxels at 1 mm, a 32-loop cylindrical coil with 2048
-segments at 298.2 MHz, ACA at tol 1e-5 by Algorithm 3 with U's tensors compressed by the
-certified fixed-width randomized Tucker (tol 3e-5, complex64 storage), 32 right-hand sides.
-One step = one Z X plus one Z^H Phi.  Metric = algorithmic TFLOP/s of the step (Table III count,
-complex MAC = 8 flops, summed over both products), with the step time and the relative error
-against the FP64 oracle on sampled outputs.  The line also carries, under "extra", the
-96^3 / 1024-segment / 16-RHS workload ("precision"), the mixed right-hand-side batches of the
-160 x 160 x 128 ACA workload ("batching") and the compression comparison of the 128^3 workload
-("learned": HOSVD against the randomized Tucker with learned and with fixed widths).
+segments at 298.2 MHz, each column stored in Tucker form at tol 1e-5 by the certified fixed-width
+randomized Tucker (HOSVD fallback; complex64 storage; Algorithm 3's ACA does not compress this
+coil's coupling matrix at that tolerance), 32 right-hand sides.  One step = one Z X plus one
+Z^H Phi.  Metric = algorithmic TFLOP/s of the step (Table III count, complex MAC = 8 flops, summed
+over both products), with the step time and the relative error against the FP64 oracle on sampled
+outputs.  The line also carries, under "extra", the 96^3 / 1024-segment / 16-RHS workload
+("precision"), the compression comparison of the 128^3 workload ("learned": HOSVD against the
+randomized Tucker with learned and with fixed widths) and the mixed right-hand-side batches of the
+160 x 160 x 128 workload ("batching"), each started only inside --extras-budget seconds.
 Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zbc|reference]
                   [--workload large|precision] [--no-extras] [--prec auto|...]
+                  [--columns N] [--n3 N] [--extras-budget S]
 
 Multi-GPU: replicas only (each rank runs the whole workload; no collective on the data path).
 """
@@ -471,16 +473,18 @@ def measure_products(h, w, zbc, torch, X, Phi, args, ws, local, nrows, npsi):
         Yh = torch.empty(Yd.shape, dtype=Yd.dtype).pin_memory()
         Psih = torch.empty(Psid.shape, dtype=Psid.dtype).pin_memory()
         # the copies run on a second stream where the data flow allows: Phi's upload beside the
-        # forward product, Y's download beside the adjoint; the step ends when every copy has
+        # forward product, Y's download beside the adjoint; the step ends when every copy has.
+        # X goes up first: host-to-device copies share one copy engine in issue order, so an X
+        # upload issued after Phi's would hold the forward back for the whole of Phi's upload.
         copy_stream = torch.cuda.Stream()
 
         def e2e_step():
             main = torch.cuda.current_stream()
+            Xd.copy_(Xh, non_blocking=True)
             copy_stream.wait_stream(main)            # the previous step is done with Phi and Y
             with torch.cuda.stream(copy_stream):
                 Phid.copy_(Phih, non_blocking=True)
             phi_ready = copy_stream.record_event()
-            Xd.copy_(Xh, non_blocking=True)
             zbc.zbc_matvec(h, Xd, Yd, fcode)
             copy_stream.wait_stream(main)
             with torch.cuda.stream(copy_stream):
