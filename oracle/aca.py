@@ -20,9 +20,9 @@ Readings where the paper is silent or garbled:
 
 Algorithm 3 takes two optional arguments used by the GPU parity tests:
   * store=np.complex64 rounds every new Tucker tensor (core and factors) to complex64 before
-    it joins U, as a GPU handle stores them (reading R7); the arithmetic stays complex128;
+    it joins U, as a GPU handle stores them; the arithmetic stays complex128;
   * trace=True records, per iteration, the residual row r and column x the pivots were taken
-    from, so that a test can tell pivots decided by a clear margin from near-ties (reading R14).
+    from, so that a test can tell pivots decided by a clear margin from near-ties.
 """
 import numpy as np
 

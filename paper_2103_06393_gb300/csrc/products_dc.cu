@@ -14,7 +14,7 @@
 //                     rows of X' as [[Re X, Im X], [-Im X, Re X]] (fp16 hi / lo, built per call):
 //                     three products (hi.hi, hi.lo, lo.hi), M = 128, N = 2P, K = 16, D in TMEM;
 //   every kDcSeg chunks the generator warps add D into an FP32 sum S in TMEM with
-//   round-to-nearest adds (the tensor core's own accumulation is not round-to-nearest, reading R6),
+//   round-to-nearest adds (the tensor core's own FP32 accumulation does not round to nearest),
 //   and after the last chunk they write Y = S scaled back.
 // Decompression costs r1 complex multiply-adds per (voxel, column) on the CUDA cores, as in the
 // FP32 form; the contraction, q n_v M p complex MACs, runs on the tensor cores with N up to 256

@@ -78,7 +78,7 @@ def test_aca_dense_masked_rows_and_products():
     assert e.max() < 1e-5
 
 
-# Reading R14 (Algorithm 3 on the GPU against the oracle).  The GPU stores U's tensors in
+# Algorithm 3 on the GPU against the oracle.  The GPU stores U's tensors in
 # complex64 and forms the residual column with Algorithm 1 in FP32, so its residuals differ from
 # the oracle's (which stores the same complex64 roundings, store=np.complex64) by rounding: an
 # entry whose value is a sum of terms of absolute size S moves by at most K_ERR * 2^-24 * S.
@@ -102,7 +102,7 @@ def _abs_columns(tens, shape):
 
 
 def _pick(vals, scale, excluded):
-    """(argmax |vals| over the allowed entries, whether it is decided by the R14 margin)."""
+    """(argmax |vals| over the allowed entries, whether the storage-error margin decides it)."""
     a = np.abs(vals).astype(np.float64)
     if excluded:
         a[list(excluded)] = -np.inf
@@ -112,9 +112,10 @@ def _pick(vals, scale, excluded):
 
 
 def _check_alg3_against_oracle(w, g, s, Z, tol, h, st, piv, Ut, Vt, info, rank_tie=1e-5, min_decided=3):
-    """Pivots bit-exact up to the first step the R14 margin does not decide, r_c exact without a
-    near-tie and within R_WINDOW after one; the approximation error tracks tol.  A Tucker rank of
-    a new column's tensors decided within rank_tie of its threshold (reading C6: 1e-5 for the
+    """Pivots bit-exact up to the first step whose argmax margin does not decide it against the
+    complex64 storage error, r_c exact without a near-tie and within R_WINDOW after one; the
+    approximation error tracks tol.  A Tucker rank of a new column's tensors decided within
+    rank_tie of its threshold (relative: 1e-5 for the
     HOSVD; 1e-3 for the randomized Tucker, whose budget tol^2 ||A||^2 - e^2 carries the rounding
     of e^2) is a near-tie too: the steps after it are not compared."""
     assert st.row_restarts == 0
@@ -122,7 +123,7 @@ def _check_alg3_against_oracle(w, g, s, Z, tol, h, st, piv, Ut, Vt, info, rank_t
     absU = _abs_columns(tens, g.shape)
     opiv = [tuple(p) for p in info["pivots"]]
     used_r, used_c = {0}, set()
-    decided = 0          # leading pivots the R14 margin decides
+    decided = 0          # leading pivots the storage-error margin decides
     tie = False
     why = ""
     for k, (i, j) in enumerate(opiv):

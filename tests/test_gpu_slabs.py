@@ -1,7 +1,7 @@
 """Voxel-slab sharding through the real product kernels, on one GPU: every rank's slab handle is
 built in turn (paper_2103_06393_gb300/shard.py), its zbc_matvec must give the unsharded product's
 rows of its slab and the sum of the ranks' zbc_rmatvec partials the unsharded adjoint, both within
-1e-5 per right-hand side of the FP64 oracle on the original tensors (reading C11)."""
+1e-5 per right-hand side of the FP64 oracle on the original tensors."""
 import numpy as np
 import pytest
 

@@ -77,7 +77,7 @@ def test_masked_start_row_is_skipped():
 
 
 def test_algorithm3_complex64_storage_and_trace():
-    """store=complex64 keeps tensors that are exactly complex64 values (reading R7), still tracks
+    """store=complex64 keeps tensors that are exactly complex64 values, still tracks
     the tolerance, and the trace's residuals are Algorithm 3's: x_k = Z[:, j_k] - U_{<k} V[j_k, <k]^H
     on the stored tensors, and r_k = Z[i_k, :] - U_{<k}[i_k, :] V_{<k}^H by element-wise evaluation."""
     g, Z = _green_case()

@@ -61,7 +61,7 @@ def test_noalloc_matches_rmatvec_twice(aca):
         zbc.zbc_product_status(h)             # synchronises; raises if a device wait gave up
         got = zbc.from_colmajor(out)
         assert _rel(got, r) < RTOL            # the allocating entry point
-        assert _rel(got, ref_o) < RTOL        # the FP64 oracle (reading C11: per right-hand side)
+        assert _rel(got, ref_o) < RTOL        # the FP64 oracle (relative error per right-hand side)
 
 
 def test_noalloc_requires_built_cache():
