@@ -441,6 +441,8 @@ int zbc_rmatvec_noalloc(const zbc_handle* h, const void* Phi, int64_t ldphi, int
  * more than 1.5 times the best of its direction so far (the tensor-core forms are timed first).
  * Afterwards the per-handle operands of the forms that no tuned class selects (TC_MODE1's, TC_DC's,
  * TC2's) are freed; a later call of such a form builds them again (zbc_device_bytes shows both).
+ * A CUDA graph captured before this call may hold pointers to those operands: tune first, then
+ * capture.
  *   times_ms_host : optional float[10], the variants' times in the order above (ms per call;
  *                   +inf for a variant that does not fit this handle)
  * Allocates scratch operands and synchronises `stream`: call it before any graph capture.
