@@ -1,7 +1,6 @@
 """GPU parity of the C-ABI path against the FP64 oracle: assembly, HOSVD compression and the
 FP32 SIMT products (Algorithms 1 and 2), with ragged grids, several right-hand-side counts,
 ACA storage, checkpoints and error statuses."""
-import os
 
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ the HOSVD fallback, and the learned-width pipeline end to end."""
 import numpy as np
 import pytest
 
-from oracle import greens, mlp, randomized, tucker
+from oracle import mlp, randomized, tucker
 from paper_2103_06393_gb300 import inputs
 
 pytestmark = pytest.mark.gpu

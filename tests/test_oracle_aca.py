@@ -1,6 +1,5 @@
 """Pins of the oracle's ACA and Algorithm 3 (Sec. II.B.2, Sec. III.C)."""
 import numpy as np
-import pytest
 
 from oracle import aca, greens, products, tucker
 from paper_2103_06393_gb300 import inputs
